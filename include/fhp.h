@@ -1,0 +1,165 @@
+/*
+ * fhp.h -- C ABI of the GB300 FHP lattice-gas library (libfhp_gb300.so).
+ *
+ * The library advances a Frisch-Hasslacher-Pomeau lattice gas: a triangular
+ * lattice whose nodes carry seven occupation bits (six moving directions and
+ * one rest particle) plus a solid flag, updated by motion, scattering with
+ * bounce-back on solid nodes, and horizontal momentum forcing
+ * (Szkoda, Koza & Tykierko, arXiv:1208.2428, Section 2).
+ *
+ * Conventions shared by every call:
+ *   - Node byte (paper Section 2, Fig. 1): bit i (i = 0..5) is a particle with
+ *     velocity c_i at angle (i-2)*60 degrees (0 SW, 1 SE, 2 E, 3 NE, 4 NW,
+ *     5 W), bit 6 is the rest particle, bit 7 marks a solid node.
+ *   - Host lattice arrays are H x W bytes, row-major (row y, then x); row
+ *     y = 0 is the bottom row and odd rows are shifted half a cell to the
+ *     right (paper Section 2, Fig. 3).  W is a positive multiple of 32 and H
+ *     is even and >= 2.  The lattice is periodic in x and y; walls are solid
+ *     rows.
+ *   - Every call returns an int status: FHP_OK (0) or one of the FHP_E*
+ *     codes below.  No call aborts or throws; CUDA errors are captured and
+ *     reported.  fhp_last_error() returns a message for the last failure.
+ *   - Pointers named host_* are host memory owned by the caller; pointers
+ *     named device_* are device memory of the lattice's device, owned by the
+ *     caller.  The library never keeps a caller pointer after a call returns,
+ *     except params->device_memory (see fhp_create).
+ *   - Calls enqueue work on the lattice's stream.  Calls that read or write
+ *     host buffers return only when the data is complete; calls taking
+ *     device buffers are asynchronous with respect to the host.
+ *   - A handle must not be used by two host threads at the same time.
+ */
+#ifndef FHP_GB300_H
+#define FHP_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define FHP_API __attribute__((visibility("default")))
+#else
+#define FHP_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FHP_OK 0
+#define FHP_EINVAL 1   /* invalid argument (sizes, NULL pointers, ranges) */
+#define FHP_ENOMEM 2   /* device or host allocation failed, or caller memory too small */
+#define FHP_ECUDA 3    /* a CUDA runtime call failed */
+#define FHP_ETIMEOUT 4 /* a bounded device-side wait gave up */
+#define FHP_EBUSY 5    /* the object is in use */
+
+typedef struct fhp_lattice fhp_lattice;
+
+typedef struct fhp_params {
+    int32_t width;              /* W: nodes per row; multiple of 32, >= 32 */
+    int32_t height;             /* H: rows; even, >= 2 */
+    uint64_t seed;              /* key of the counter-based random generator */
+    double forcing_p;           /* forcing probability per candidate node, in [0, 1] */
+    void* stream;               /* cudaStream_t to enqueue on; NULL = legacy default stream */
+    void* device_memory;        /* optional caller-owned device memory, 256-byte aligned,
+                                   at least fhp_required_bytes(W, H); NULL = library allocates */
+    size_t device_memory_bytes; /* size of device_memory in bytes */
+} fhp_params;
+
+/* Bytes of device memory one lattice of W x H nodes uses: two bit-plane
+ * state buffers (7 planes each), one solid plane, and a W*H-byte staging
+ * area for transfers and coarse-grained results.  Returns 0 for invalid
+ * sizes. */
+FHP_API size_t fhp_required_bytes(int32_t width, int32_t height);
+
+/* Create a lattice on the current CUDA device with all nodes empty and
+ * fluid, at step t = 0.  If params->device_memory is not NULL the library
+ * uses that memory and the caller must keep it alive until fhp_destroy;
+ * otherwise the library allocates and frees its own.  On failure *out is set
+ * to NULL and fhp_last_error(NULL) describes the error. */
+FHP_API int fhp_create(fhp_lattice** out, const fhp_params* params);
+
+/* Release the lattice and any memory the library allocated.  Waits for work
+ * queued on the lattice's stream.  NULL is accepted and ignored. */
+FHP_API void fhp_destroy(fhp_lattice* lattice);
+
+/* Message for the last failed call on `lattice`, or of the calling thread's
+ * last failed fhp_create when `lattice` is NULL.  Never NULL; "" if none. */
+FHP_API const char* fhp_last_error(const fhp_lattice* lattice);
+
+/* Replace the whole lattice state, solid flags included (bit 7), from H x W
+ * host bytes (paper Section 2, Fig. 1).  Particles on solid nodes are kept:
+ * under bounce-back a solid node holds reflected particles for one step, so
+ * a saved state round-trips exactly.  Synchronous. */
+FHP_API int fhp_set_state(fhp_lattice* lattice, const uint8_t* host_bytes);
+
+/* Copy the whole lattice state into H x W host bytes (same layout as
+ * fhp_set_state).  Synchronous. */
+FHP_API int fhp_get_state(fhp_lattice* lattice, uint8_t* host_bytes);
+
+/* As fhp_set_state / fhp_get_state with H x W bytes in device memory of the
+ * lattice's device.  fhp_get_state_device is asynchronous on the lattice's
+ * stream; fhp_set_state_device returns once the state is packed, because it
+ * reads back whether any node is solid (that selects the step kernel). */
+FHP_API int fhp_set_state_device(fhp_lattice* lattice, const uint8_t* device_bytes);
+FHP_API int fhp_get_state_device(fhp_lattice* lattice, uint8_t* device_bytes);
+
+/* Replace the solid map from an H x W host mask (nonzero = solid) and clear
+ * the particles of every node that is solid in the new map (paper Section 2:
+ * boundary nodes carry bit 7 and reflect particles).  Synchronous. */
+FHP_API int fhp_load_obstacles(fhp_lattice* lattice, const uint8_t* host_mask);
+
+/* Advance the lattice by n >= 0 time steps.  One step is motion, then
+ * scattering through the FHP-II rules with bounce-back on solid nodes, then
+ * forcing (paper Section 2).  Random chirality and forcing draws depend only
+ * on (seed, step, node), so results do not depend on how steps are grouped
+ * into calls or kernel launches.  Asynchronous on the lattice's stream.
+ * t + n must stay below 2^48. */
+FHP_API int fhp_step(fhp_lattice* lattice, int64_t n);
+
+/* Coarse-grain the current state over B x B blocks (B a multiple of 32 that
+ * divides W and H).  For block (by, bx), at index c = by * (W/B) + bx:
+ *   counts[9c + i], i = 0..6: fluid nodes of the block with bit i set;
+ *   counts[9c + 7]: fluid nodes; counts[9c + 8]: particles on fluid nodes;
+ *   rho[c] = mass / fluid nodes; ux[c] = jx2 / (2 mass);
+ *   uy[c] = (sqrt(3)/2) jy / mass, with jx2 = sum_i n_i 2cos(theta_i) and
+ *   jy = sum_i n_i sgn(sin(theta_i)); 0 where the denominator is 0.
+ * Host buffers; any output may be NULL.  Synchronous. */
+FHP_API int fhp_coarse_grain(fhp_lattice* lattice, int32_t block, int32_t* host_counts,
+                     float* host_rho, float* host_ux, float* host_uy);
+
+/* As fhp_coarse_grain with device buffers (none may be NULL).
+ * Asynchronous on the lattice's stream. */
+FHP_API int fhp_coarse_grain_device(fhp_lattice* lattice, int32_t block, int32_t* device_counts,
+                            float* device_rho, float* device_ux, float* device_uy);
+
+/* Current step counter t (number of steps applied since t = 0). */
+FHP_API int64_t fhp_get_time(const fhp_lattice* lattice);
+
+/* Set the step counter (for resuming a saved run); 0 <= t < 2^48. */
+FHP_API int fhp_set_time(fhp_lattice* lattice, int64_t t);
+
+/* Change the forcing probability (in [0, 1]) for subsequent steps. */
+FHP_API int fhp_set_forcing(fhp_lattice* lattice, double p);
+
+/* Number of steps fused into one kernel pass (temporal blocking): 1, 2, 4
+ * or 8.  Results are identical for every value.  Default 1. */
+FHP_API int fhp_set_temporal_block(fhp_lattice* lattice, int32_t k);
+
+/* Block the calling thread until all work queued on the lattice's stream
+ * has finished; reports asynchronous CUDA errors. */
+FHP_API int fhp_synchronize(fhp_lattice* lattice);
+
+/* Number of kernel launches this lattice has issued since creation. */
+FHP_API int64_t fhp_kernel_launches(const fhp_lattice* lattice);
+
+/* Diagnostic: Philox4x32-10 (Salmon et al., SC'11) evaluated by the
+ * library's device code.  device_ctr holds n counters of 4 words,
+ * device_key n keys of 2 words, device_out receives n blocks of 4 words.
+ * Asynchronous on `stream` (cudaStream_t, NULL = legacy default stream). */
+FHP_API int fhp_philox4x32_10_device(const uint32_t* device_ctr, const uint32_t* device_key,
+                             uint32_t* device_out, int64_t n, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FHP_GB300_H */

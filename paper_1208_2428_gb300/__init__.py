@@ -1,0 +1,9 @@
+"""GB300-native FHP lattice gas (arXiv:1208.2428 hot path).
+
+The update runs in hand-written CUDA for sm_103a behind the C ABI of
+``include/fhp.h``; this package holds the CUDA sources (``csrc/``), their
+build (``build.py``) and the ctypes binding (``fhp.py``).
+"""
+from .fhp import FhpError, Lattice, load, philox4x32_10_device, required_bytes  # noqa: F401
+
+__all__ = ["FhpError", "Lattice", "load", "philox4x32_10_device", "required_bytes"]

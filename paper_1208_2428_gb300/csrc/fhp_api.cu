@@ -1,0 +1,369 @@
+// fhp_api.cu -- the extern "C" boundary declared in include/fhp.h.
+//
+// Owns lattice handles (geometry, device buffers, step counter, stream),
+// validates arguments, turns CUDA errors into status codes and messages, and
+// sequences the kernels of fhp_step.cu, fhp_pack.cu and fhp_coarse.cu.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "../../include/fhp.h"
+#include "fhp_internal.h"
+
+struct fhp_lattice {
+    fhp::Geometry g;
+    uint64_t seed = 0;
+    double p = 0.0;
+    fhp::ForcingTable ft{};
+    bool force = false;
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    bool owns_memory = false;
+    uint8_t* base = nullptr;
+    size_t bytes = 0;
+    uint32_t* buf[2] = {nullptr, nullptr};
+    uint32_t* solid = nullptr;
+    unsigned int* flags = nullptr;  // device word: any solid node
+    uint8_t* staging = nullptr;
+    size_t staging_bytes = 0;
+    int cur = 0;
+    int64_t t = 0;
+    bool has_solid = false;
+    int k_block = 1;
+    int64_t launches = 0;
+    std::string err;
+};
+
+namespace {
+
+constexpr int64_t kMaxTime = (int64_t)1 << 48;
+thread_local std::string g_create_error;
+
+size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+int fail(fhp_lattice* h, int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (h) h->err = buf; else g_create_error = buf;
+    return code;
+}
+
+int cuda_fail(fhp_lattice* h, cudaError_t e, const char* what) {
+    return fail(h, FHP_ECUDA, "%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
+}
+
+bool valid_size(int32_t W, int32_t H) {
+    return W >= 32 && W % 32 == 0 && H >= 2 && H % 2 == 0 && (int64_t)W * H <= ((int64_t)1 << 40);
+}
+
+struct Layout {
+    size_t plane_bytes, state_bytes, solid_off, flags_off, staging_off, staging_bytes, total;
+};
+
+Layout layout(int32_t W, int32_t H) {
+    const fhp::Geometry g = fhp::make_geometry(W, H);
+    Layout L;
+    L.plane_bytes = round_up(g.plane_words * sizeof(uint32_t), 256);
+    L.state_bytes = 7 * L.plane_bytes;
+    L.solid_off = 2 * L.state_bytes;
+    L.flags_off = L.solid_off + L.plane_bytes;
+    L.staging_off = L.flags_off + 256;
+    L.staging_bytes = round_up((size_t)W * H, 256);
+    L.total = L.staging_off + L.staging_bytes;
+    return L;
+}
+
+// Forcing thresholds: P = round-half-even(p * 2^32); S_0 = 2^32,
+// S_g = floor(S_{g-1} (2^32 - P) / 2^32); Q_g = 2^32 - S_g.
+fhp::ForcingTable forcing_table(double p) {
+    const unsigned long long one = 1ULL << 32;
+    unsigned long long P;
+    const double scaled = std::ldexp(p, 32);
+    if (!(scaled > 0.0)) P = 0;
+    else if (scaled >= std::ldexp(1.0, 32)) P = one;
+    else P = (unsigned long long)std::nearbyint(scaled);  // default mode: nearest, ties to even
+    fhp::ForcingTable ft;
+    unsigned long long S = one;
+    ft.q[0] = 0;
+    for (int g = 1; g <= 32; ++g) {
+        S = (unsigned long long)(((unsigned __int128)S * (one - P)) >> 32);
+        ft.q[g] = one - S;
+    }
+    return ft;
+}
+
+// Makes the lattice's device current for the duration of a call.
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+        else if (prev == dev) prev = -1;
+    }
+    ~DeviceGuard() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+int check_block(fhp_lattice* h, int32_t B) {
+    if (B < 32 || B % 32 != 0 || h->g.W % B != 0 || h->g.H % B != 0)
+        return fail(h, FHP_EINVAL, "coarse-grain block %d must be a multiple of 32 dividing W=%d and H=%d",
+                    B, h->g.W, h->g.H);
+    return FHP_OK;
+}
+
+int read_solid_flag(fhp_lattice* h) {
+    unsigned int flag = 0;
+    cudaError_t e = cudaMemcpyAsync(&flag, h->flags, sizeof flag, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "reading the solid flag");
+    h->has_solid = flag != 0;
+    return FHP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t fhp_required_bytes(int32_t width, int32_t height) {
+    if (!valid_size(width, height)) return 0;
+    return layout(width, height).total;
+}
+
+int fhp_create(fhp_lattice** out, const fhp_params* params) {
+    if (!out) return fail(nullptr, FHP_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!params) return fail(nullptr, FHP_EINVAL, "params is NULL");
+    const int32_t W = params->width, H = params->height;
+    if (!valid_size(W, H))
+        return fail(nullptr, FHP_EINVAL, "invalid lattice %d x %d: W must be a positive multiple of 32, H even >= 2",
+                    W, H);
+    if (!(params->forcing_p >= 0.0 && params->forcing_p <= 1.0))
+        return fail(nullptr, FHP_EINVAL, "forcing probability %g outside [0, 1]", params->forcing_p);
+    fhp_lattice* h = new (std::nothrow) fhp_lattice();
+    if (!h) return fail(nullptr, FHP_ENOMEM, "host allocation failed");
+    cudaError_t e = cudaGetDevice(&h->device);
+    if (e != cudaSuccess) {
+        delete h;
+        return fail(nullptr, FHP_ECUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
+    }
+    h->g = fhp::make_geometry(W, H);
+    h->seed = params->seed;
+    h->p = params->forcing_p;
+    h->ft = forcing_table(h->p);
+    h->force = h->ft.q[32] != 0;
+    h->stream = (cudaStream_t)params->stream;
+    const Layout L = layout(W, H);
+    if (params->device_memory) {
+        if (params->device_memory_bytes < L.total || ((uintptr_t)params->device_memory & 255u)) {
+            delete h;
+            return fail(nullptr, FHP_ENOMEM, "device_memory must be 256-byte aligned and hold %zu bytes (got %zu)",
+                        L.total, params->device_memory_bytes);
+        }
+        h->base = (uint8_t*)params->device_memory;
+        h->owns_memory = false;
+    } else {
+        e = cudaMalloc((void**)&h->base, L.total);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            delete h;
+            return fail(nullptr, FHP_ENOMEM, "cudaMalloc(%zu): %s", L.total, cudaGetErrorString(e));
+        }
+        h->owns_memory = true;
+    }
+    h->bytes = L.total;
+    h->buf[0] = (uint32_t*)h->base;
+    h->buf[1] = (uint32_t*)(h->base + L.state_bytes);
+    h->solid = (uint32_t*)(h->base + L.solid_off);
+    h->flags = (unsigned int*)(h->base + L.flags_off);
+    h->staging = h->base + L.staging_off;
+    h->staging_bytes = L.staging_bytes;
+    // Empty fluid lattice: zero both buffers and the solid plane.
+    e = cudaMemsetAsync(h->base, 0, L.staging_off, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) {
+        if (h->owns_memory) cudaFree(h->base);
+        delete h;
+        return fail(nullptr, FHP_ECUDA, "initialising device memory: %s", cudaGetErrorString(e));
+    }
+    *out = h;
+    return FHP_OK;
+}
+
+void fhp_destroy(fhp_lattice* h) {
+    if (!h) return;
+    DeviceGuard dg(h->device);
+    cudaStreamSynchronize(h->stream);
+    if (h->owns_memory && h->base) cudaFree(h->base);
+    delete h;
+}
+
+const char* fhp_last_error(const fhp_lattice* h) {
+    return h ? h->err.c_str() : g_create_error.c_str();
+}
+
+int fhp_set_state(fhp_lattice* h, const uint8_t* host_bytes) {
+    if (!h) return fail(nullptr, FHP_EINVAL, "lattice is NULL");
+    if (!host_bytes) return fail(h, FHP_EINVAL, "host_bytes is NULL");
+    DeviceGuard dg(h->device);
+    const size_t n = (size_t)h->g.W * h->g.H;
+    cudaError_t e = cudaMemcpyAsync(h->staging, host_bytes, n, cudaMemcpyHostToDevice, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "copying the state to the device");
+    return fhp_set_state_device(h, h->staging);
+}
+
+int fhp_set_state_device(fhp_lattice* h, const uint8_t* device_bytes) {
+    if (!h) return fail(nullptr, FHP_EINVAL, "lattice is NULL");
+    if (!device_bytes) return fail(h, FHP_EINVAL, "device_bytes is NULL");
+    DeviceGuard dg(h->device);
+    cudaError_t e = cudaMemsetAsync(h->flags, 0, sizeof(unsigned int), h->stream);
+    if (e == cudaSuccess) e = fhp::launch_pack(h->g, device_bytes, h->buf[h->cur], h->solid, h->flags, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "packing the state");
+    ++h->launches;
+    return read_solid_flag(h);
+}
+
+int fhp_get_state(fhp_lattice* h, uint8_t* host_bytes) {
+    if (!h) return fail(nullptr, FHP_EINVAL, "lattice is NULL");
+    if (!host_bytes) return fail(h, FHP_EINVAL, "host_bytes is NULL");
+    DeviceGuard dg(h->device);
+    int rc = fhp_get_state_device(h, h->staging);
+    if (rc != FHP_OK) return rc;
+    const size_t n = (size_t)h->g.W * h->g.H;
+    cudaError_t e = cudaMemcpyAsync(host_bytes, h->staging, n, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "copying the state to the host");
+    return FHP_OK;
+}
+
+int fhp_get_state_device(fhp_lattice* h, uint8_t* device_bytes) {
+    if (!h) return fail(nullptr, FHP_EINVAL, "lattice is NULL");
+    if (!device_bytes) return fail(h, FHP_EINVAL, "device_bytes is NULL");
+    DeviceGuard dg(h->device);
+    cudaError_t e = fhp::launch_unpack(h->g, h->buf[h->cur], h->solid, device_bytes, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "unpacking the state");
+    ++h->launches;
+    return FHP_OK;
+}
+
+int fhp_load_obstacles(fhp_lattice* h, const uint8_t* host_mask) {
+    if (!h) return fail(nullptr, FHP_EINVAL, "lattice is NULL");
+    if (!host_mask) return fail(h, FHP_EINVAL, "host_mask is NULL");
+    DeviceGuard dg(h->device);
+    const size_t n = (size_t)h->g.W * h->g.H;
+    cudaError_t e = cudaMemcpyAsync(h->staging, host_mask, n, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->flags, 0, sizeof(unsigned int), h->stream);
+    if (e == cudaSuccess)
+        e = fhp::launch_load_obstacles(h->g, h->staging, h->buf[h->cur], h->solid, h->flags, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "loading obstacles");
+    ++h->launches;
+    return read_solid_flag(h);
+}
+
+int fhp_step(fhp_lattice* h, int64_t n) {
+    if (!h) return fail(nullptr, FHP_EINVAL, "lattice is NULL");
+    if (n < 0) return fail(h, FHP_EINVAL, "negative step count %lld", (long long)n);
+    if (n > kMaxTime - h->t) return fail(h, FHP_EINVAL, "step counter would pass 2^48");
+    DeviceGuard dg(h->device);
+    const fhp::Key2 key{(uint32_t)h->seed, (uint32_t)(h->seed >> 32)};
+    for (int64_t i = 0; i < n; ++i) {
+        cudaError_t e = fhp::launch_step(h->g, h->buf[h->cur], h->buf[h->cur ^ 1], h->solid, h->has_solid,
+                                         h->force, h->ft, key, (uint64_t)h->t, h->stream);
+        if (e != cudaSuccess) return cuda_fail(h, e, "launching the step kernel");
+        ++h->launches;
+        h->cur ^= 1;
+        ++h->t;
+    }
+    return FHP_OK;
+}
+
+int fhp_coarse_grain(fhp_lattice* h, int32_t block, int32_t* counts, float* rho, float* ux, float* uy) {
+    if (!h) return fail(nullptr, FHP_EINVAL, "lattice is NULL");
+    int rc = check_block(h, block);
+    if (rc != FHP_OK) return rc;
+    DeviceGuard dg(h->device);
+    const size_t cells = (size_t)(h->g.W / block) * (h->g.H / block);
+    int32_t* d_counts = (int32_t*)h->staging;
+    float* d_rho = (float*)(h->staging + round_up(cells * 9 * sizeof(int32_t), 256));
+    float* d_ux = (float*)((uint8_t*)d_rho + round_up(cells * sizeof(float), 256));
+    float* d_uy = (float*)((uint8_t*)d_ux + round_up(cells * sizeof(float), 256));
+    rc = fhp_coarse_grain_device(h, block, d_counts, d_rho, d_ux, d_uy);
+    if (rc != FHP_OK) return rc;
+    cudaError_t e = cudaSuccess;
+    if (counts && e == cudaSuccess)
+        e = cudaMemcpyAsync(counts, d_counts, cells * 9 * sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream);
+    if (rho && e == cudaSuccess)
+        e = cudaMemcpyAsync(rho, d_rho, cells * sizeof(float), cudaMemcpyDeviceToHost, h->stream);
+    if (ux && e == cudaSuccess)
+        e = cudaMemcpyAsync(ux, d_ux, cells * sizeof(float), cudaMemcpyDeviceToHost, h->stream);
+    if (uy && e == cudaSuccess)
+        e = cudaMemcpyAsync(uy, d_uy, cells * sizeof(float), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "copying coarse-grained fields to the host");
+    return FHP_OK;
+}
+
+int fhp_coarse_grain_device(fhp_lattice* h, int32_t block, int32_t* counts, float* rho, float* ux, float* uy) {
+    if (!h) return fail(nullptr, FHP_EINVAL, "lattice is NULL");
+    int rc = check_block(h, block);
+    if (rc != FHP_OK) return rc;
+    if (!counts || !rho || !ux || !uy) return fail(h, FHP_EINVAL, "device outputs must not be NULL");
+    DeviceGuard dg(h->device);
+    cudaError_t e = fhp::launch_coarse_grain(h->g, h->buf[h->cur], h->solid, h->has_solid, block, counts, rho,
+                                             ux, uy, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "launching the coarse-grain kernel");
+    ++h->launches;
+    return FHP_OK;
+}
+
+int64_t fhp_get_time(const fhp_lattice* h) { return h ? h->t : -1; }
+
+int fhp_set_time(fhp_lattice* h, int64_t t) {
+    if (!h) return fail(nullptr, FHP_EINVAL, "lattice is NULL");
+    if (t < 0 || t >= kMaxTime) return fail(h, FHP_EINVAL, "step counter %lld outside [0, 2^48)", (long long)t);
+    h->t = t;
+    return FHP_OK;
+}
+
+int fhp_set_forcing(fhp_lattice* h, double p) {
+    if (!h) return fail(nullptr, FHP_EINVAL, "lattice is NULL");
+    if (!(p >= 0.0 && p <= 1.0)) return fail(h, FHP_EINVAL, "forcing probability %g outside [0, 1]", p);
+    h->p = p;
+    h->ft = forcing_table(p);
+    h->force = h->ft.q[32] != 0;
+    return FHP_OK;
+}
+
+int fhp_set_temporal_block(fhp_lattice* h, int32_t k) {
+    if (!h) return fail(nullptr, FHP_EINVAL, "lattice is NULL");
+    if (k != 1 && k != 2 && k != 4 && k != 8) return fail(h, FHP_EINVAL, "temporal block %d not in {1,2,4,8}", k);
+    h->k_block = k;
+    return FHP_OK;
+}
+
+int fhp_synchronize(fhp_lattice* h) {
+    if (!h) return fail(nullptr, FHP_EINVAL, "lattice is NULL");
+    DeviceGuard dg(h->device);
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "synchronizing");
+    return FHP_OK;
+}
+
+int64_t fhp_kernel_launches(const fhp_lattice* h) { return h ? h->launches : -1; }
+
+int fhp_philox4x32_10_device(const uint32_t* ctr, const uint32_t* key, uint32_t* out, int64_t n, void* stream) {
+    if (!ctr || !key || !out || n < 0) return fail(nullptr, FHP_EINVAL, "invalid Philox arguments");
+    if (n == 0) return FHP_OK;
+    cudaError_t e = fhp::launch_philox(ctr, key, out, n, (cudaStream_t)stream);
+    if (e != cudaSuccess) return fail(nullptr, FHP_ECUDA, "Philox kernel: %s", cudaGetErrorString(e));
+    return FHP_OK;
+}
+
+}  // extern "C"

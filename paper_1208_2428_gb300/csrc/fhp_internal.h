@@ -1,0 +1,81 @@
+// fhp_internal.h -- layout and launcher declarations shared by the library's
+// translation units (not part of the public ABI).
+//
+// Device layout of one lattice of W x H nodes (W multiple of 32, H even):
+//   Wq = W / 32 words per row, nq = ceil(Wq / 4) quads of 4 words per row,
+//   row pitch Pq = 4 * nq words (16-byte aligned rows; the words Wq..Pq-1 of
+//   every row are padding and stay zero).  A plane is H * Pq words; a state
+//   buffer is 7 consecutive planes (planes 0..5 movers along c_0..c_5,
+//   plane 6 rest particles); the solid flags form one more plane.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+
+namespace fhp {
+
+struct Key2 {
+    uint32_t lo, hi;
+};
+
+struct ForcingTable {
+    unsigned long long q[33];
+};
+
+struct Geometry {
+    int W = 0, H = 0;
+    int Wq = 0;         // words per row
+    int nq = 0;         // quads per row
+    int Pq = 0;         // row pitch in words (multiple of 4)
+    size_t plane_words = 0;  // H * Pq
+};
+
+Geometry make_geometry(int W, int H);
+
+// Arguments of one k = 1 step kernel launch.
+struct StepArgs {
+    const uint32_t* __restrict__ src;    // 7 planes of S_t
+    uint32_t* __restrict__ dst;          // 7 planes of S_{t+1}
+    const uint32_t* __restrict__ solid;  // solid plane (read only if has_solid)
+    unsigned long long plane_words;
+    int H, Wq, nq, Pq;
+    int rows_per_warp;       // nq < 32: rows of one parity packed into a warp
+    int groups_per_parity;   // nq < 32: warps per row parity
+    int warps_per_row;       // nq >= 32: warps covering one row
+    Key2 key;
+    uint32_t t_lo, t_hi;
+    ForcingTable ft;
+};
+
+// Launch one time step (motion, scattering, bounce-back, forcing).
+cudaError_t launch_step(const Geometry& g, const uint32_t* src, uint32_t* dst,
+                        const uint32_t* solid, bool has_solid, bool force,
+                        const ForcingTable& ft, Key2 key, uint64_t t, cudaStream_t stream);
+
+// Pack H x W node bytes (device) into 7 state planes + the solid plane.
+// Sets *device_any_solid to a nonzero value if any node is solid.
+cudaError_t launch_pack(const Geometry& g, const uint8_t* bytes, uint32_t* state,
+                        uint32_t* solid, unsigned int* device_any_solid, cudaStream_t stream);
+
+// Unpack 7 state planes + the solid plane into H x W node bytes (device).
+cudaError_t launch_unpack(const Geometry& g, const uint32_t* state, const uint32_t* solid,
+                          uint8_t* bytes, cudaStream_t stream);
+
+// Replace the solid plane from an H x W byte mask (nonzero = solid) and clear
+// the particles of solid nodes in `state`.
+cudaError_t launch_load_obstacles(const Geometry& g, const uint8_t* mask, uint32_t* state,
+                                  uint32_t* solid, unsigned int* device_any_solid,
+                                  cudaStream_t stream);
+
+// Coarse-grain over B x B blocks (B multiple of 32 dividing W and H).
+cudaError_t launch_coarse_grain(const Geometry& g, const uint32_t* state, const uint32_t* solid,
+                                bool has_solid, int B, int32_t* counts, float* rho, float* ux,
+                                float* uy, cudaStream_t stream);
+
+// Philox4x32-10 over n counters (diagnostic entry point).
+cudaError_t launch_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, int64_t n,
+                          cudaStream_t stream);
+
+}  // namespace fhp

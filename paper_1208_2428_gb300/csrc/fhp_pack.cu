@@ -1,0 +1,111 @@
+// fhp_pack.cu -- conversion between node bytes (arXiv:1208.2428 Section 2,
+// Fig. 1: bits 0-5 movers, bit 6 rest, bit 7 solid) and bit-planes, and the
+// obstacle map.  One warp converts one 32-node word at a time: lane j holds
+// node 32w + j and __ballot_sync gathers bit b of the 32 nodes into plane b.
+#include "fhp_internal.h"
+
+namespace fhp {
+namespace {
+
+constexpr unsigned kFull = 0xFFFFFFFFu;
+constexpr int kBlock = 256;
+
+unsigned grid_for(size_t warps) {
+    size_t blocks = (warps * 32 + kBlock - 1) / kBlock;
+    if (blocks > 65535u * 16u) blocks = 65535u * 16u;  // grid-stride loop covers the rest
+    return (unsigned)(blocks ? blocks : 1);
+}
+
+__global__ void __launch_bounds__(kBlock) pack_kernel(Geometry g, const uint8_t* __restrict__ bytes,
+                                                      uint32_t* __restrict__ state,
+                                                      uint32_t* __restrict__ solid,
+                                                      unsigned int* __restrict__ any_solid) {
+    const int lane = threadIdx.x & 31;
+    const size_t nwarps = ((size_t)gridDim.x * blockDim.x) >> 5;
+    const size_t total = (size_t)g.H * g.Pq;
+    for (size_t item = ((size_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; item < total;
+         item += nwarps) {
+        const int y = (int)(item / g.Pq);
+        const int w = (int)(item - (size_t)y * g.Pq);
+        uint32_t v = 0;
+        if (w < g.Wq) v = bytes[(size_t)y * g.W + 32 * w + lane];
+        uint32_t mine = 0;
+#pragma unroll
+        for (int b = 0; b < 8; ++b) {
+            const uint32_t plane_word = __ballot_sync(kFull, (v >> b) & 1u);
+            if (lane == b) mine = plane_word;
+        }
+        const size_t off = (size_t)y * g.Pq + w;
+        if (lane < 7) state[(size_t)lane * g.plane_words + off] = mine;
+        if (lane == 7) {
+            solid[off] = mine;
+            if (mine) atomicOr(any_solid, 1u);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kBlock) unpack_kernel(Geometry g, const uint32_t* __restrict__ state,
+                                                        const uint32_t* __restrict__ solid,
+                                                        uint8_t* __restrict__ bytes) {
+    const int lane = threadIdx.x & 31;
+    const size_t nwarps = ((size_t)gridDim.x * blockDim.x) >> 5;
+    const size_t total = (size_t)g.H * g.Wq;
+    for (size_t item = ((size_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; item < total;
+         item += nwarps) {
+        const int y = (int)(item / g.Wq);
+        const int w = (int)(item - (size_t)y * g.Wq);
+        const size_t off = (size_t)y * g.Pq + w;
+        uint32_t byte = ((solid[off] >> lane) & 1u) << 7;
+#pragma unroll
+        for (int b = 0; b < 7; ++b) byte |= ((state[(size_t)b * g.plane_words + off] >> lane) & 1u) << b;
+        bytes[(size_t)y * g.W + 32 * w + lane] = (uint8_t)byte;
+    }
+}
+
+__global__ void __launch_bounds__(kBlock) obstacle_kernel(Geometry g, const uint8_t* __restrict__ mask,
+                                                          uint32_t* __restrict__ state,
+                                                          uint32_t* __restrict__ solid,
+                                                          unsigned int* __restrict__ any_solid) {
+    const int lane = threadIdx.x & 31;
+    const size_t nwarps = ((size_t)gridDim.x * blockDim.x) >> 5;
+    const size_t total = (size_t)g.H * g.Pq;
+    for (size_t item = ((size_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; item < total;
+         item += nwarps) {
+        const int y = (int)(item / g.Pq);
+        const int w = (int)(item - (size_t)y * g.Pq);
+        bool s = false;
+        if (w < g.Wq) s = mask[(size_t)y * g.W + 32 * w + lane] != 0;
+        const uint32_t word = __ballot_sync(kFull, s);
+        const size_t off = (size_t)y * g.Pq + w;
+        if (lane < 7 && word) state[(size_t)lane * g.plane_words + off] &= ~word;
+        if (lane == 7) {
+            solid[off] = word;
+            if (word) atomicOr(any_solid, 1u);
+        }
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_pack(const Geometry& g, const uint8_t* bytes, uint32_t* state, uint32_t* solid,
+                        unsigned int* device_any_solid, cudaStream_t stream) {
+    pack_kernel<<<grid_for((size_t)g.H * g.Pq), kBlock, 0, stream>>>(g, bytes, state, solid,
+                                                                    device_any_solid);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_unpack(const Geometry& g, const uint32_t* state, const uint32_t* solid,
+                          uint8_t* bytes, cudaStream_t stream) {
+    unpack_kernel<<<grid_for((size_t)g.H * g.Wq), kBlock, 0, stream>>>(g, state, solid, bytes);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_load_obstacles(const Geometry& g, const uint8_t* mask, uint32_t* state,
+                                  uint32_t* solid, unsigned int* device_any_solid,
+                                  cudaStream_t stream) {
+    obstacle_kernel<<<grid_for((size_t)g.H * g.Pq), kBlock, 0, stream>>>(g, mask, state, solid,
+                                                                        device_any_solid);
+    return cudaGetLastError();
+}
+
+}  // namespace fhp

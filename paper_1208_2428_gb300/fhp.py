@@ -1,0 +1,269 @@
+"""ctypes binding of the C ABI in ``include/fhp.h`` (libfhp_gb300.so).
+
+Argument marshalling only: every step of the FHP update runs in the CUDA
+library.  PyTorch supplies device memory (the lattice buffers are a torch
+allocation handed to ``fhp_create``) and the CUDA stream (torch's current
+stream).  If the library is missing this module raises; there is no CPU
+fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_lib", "libfhp_gb300.so")
+HEADER = os.path.join(os.path.dirname(_PKG), "include", "fhp.h")
+
+FHP_OK, FHP_EINVAL, FHP_ENOMEM, FHP_ECUDA, FHP_ETIMEOUT, FHP_EBUSY = range(6)
+_ERRNAMES = {1: "FHP_EINVAL", 2: "FHP_ENOMEM", 3: "FHP_ECUDA", 4: "FHP_ETIMEOUT", 5: "FHP_EBUSY"}
+
+_lib = None
+
+
+class FhpError(RuntimeError):
+    def __init__(self, code: int, message: str):
+        super().__init__(f"{_ERRNAMES.get(code, code)}: {message}")
+        self.code = code
+
+
+class _Params(ctypes.Structure):
+    _fields_ = [("width", ctypes.c_int32), ("height", ctypes.c_int32), ("seed", ctypes.c_uint64),
+                ("forcing_p", ctypes.c_double), ("stream", ctypes.c_void_p),
+                ("device_memory", ctypes.c_void_p), ("device_memory_bytes", ctypes.c_size_t)]
+
+
+def exported_names() -> list[str]:
+    """Function names declared in include/fhp.h."""
+    with open(HEADER) as f:
+        text = f.read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(fhp_[a-z0-9_]+)\s*\(", text)))
+
+
+def load(path: str | None = None):
+    """Load libfhp_gb300.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise ImportError(f"{p} is missing: build the CUDA library first "
+                          "(python -c 'import __graft_entry__ as g; g.build()')")
+    lib = ctypes.CDLL(p)
+    vp, i32, i64, u8p = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p
+    sig = {
+        "fhp_required_bytes": (ctypes.c_size_t, [i32, i32]),
+        "fhp_create": (ctypes.c_int, [ctypes.POINTER(vp), ctypes.POINTER(_Params)]),
+        "fhp_destroy": (None, [vp]),
+        "fhp_last_error": (ctypes.c_char_p, [vp]),
+        "fhp_set_state": (ctypes.c_int, [vp, u8p]),
+        "fhp_get_state": (ctypes.c_int, [vp, u8p]),
+        "fhp_set_state_device": (ctypes.c_int, [vp, u8p]),
+        "fhp_get_state_device": (ctypes.c_int, [vp, u8p]),
+        "fhp_load_obstacles": (ctypes.c_int, [vp, u8p]),
+        "fhp_step": (ctypes.c_int, [vp, i64]),
+        "fhp_coarse_grain": (ctypes.c_int, [vp, i32, vp, vp, vp, vp]),
+        "fhp_coarse_grain_device": (ctypes.c_int, [vp, i32, vp, vp, vp, vp]),
+        "fhp_get_time": (i64, [vp]),
+        "fhp_set_time": (ctypes.c_int, [vp, i64]),
+        "fhp_set_forcing": (ctypes.c_int, [vp, ctypes.c_double]),
+        "fhp_set_temporal_block": (ctypes.c_int, [vp, i32]),
+        "fhp_synchronize": (ctypes.c_int, [vp]),
+        "fhp_kernel_launches": (i64, [vp]),
+        "fhp_philox4x32_10_device": (ctypes.c_int, [vp, vp, vp, i64, vp]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _ptr(a: np.ndarray):
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+def required_bytes(width: int, height: int) -> int:
+    return int(load().fhp_required_bytes(width, height))
+
+
+class Lattice:
+    """One FHP lattice resident on a CUDA device.
+
+    ``width`` x ``height`` nodes (width a multiple of 32, height even),
+    counter-based random stream keyed by ``seed``, forcing probability
+    ``forcing_p``.  Device memory comes from torch on ``device``; work is
+    enqueued on ``stream`` (a torch.cuda.Stream, default: the current stream).
+    """
+
+    def __init__(self, width: int, height: int, seed: int = 0, forcing_p: float = 0.0,
+                 device=None, stream=None):
+        torch = _torch()
+        self._lib = load()
+        self.width, self.height = int(width), int(height)
+        self.device = torch.device("cuda", torch.cuda.current_device()) if device is None \
+            else torch.device(device)
+        nbytes = self._lib.fhp_required_bytes(self.width, self.height)
+        if nbytes == 0:
+            raise FhpError(FHP_EINVAL, f"invalid lattice {width} x {height}")
+        with torch.cuda.device(self.device):
+            self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+            self._mem = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
+            base = self._mem.data_ptr()
+            aligned = (base + 255) & ~255
+            p = _Params(self.width, self.height, int(seed) & (2**64 - 1), float(forcing_p),
+                        ctypes.c_void_p(self.stream.cuda_stream), ctypes.c_void_p(aligned), nbytes)
+            h = ctypes.c_void_p()
+            rc = self._lib.fhp_create(ctypes.byref(h), ctypes.byref(p))
+        if rc != FHP_OK:
+            raise FhpError(rc, self._lib.fhp_last_error(None).decode())
+        self._h = h
+        self.seed = int(seed)
+        self.forcing_p = float(forcing_p)
+
+    # -- plumbing -------------------------------------------------------------
+    def _check(self, rc: int):
+        if rc != FHP_OK:
+            raise FhpError(rc, self._lib.fhp_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.fhp_destroy(self._h)
+            self._h = None
+            self._mem = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @property
+    def shape(self):
+        return (self.height, self.width)
+
+    # -- state ----------------------------------------------------------------
+    def set_state(self, state: np.ndarray):
+        s = np.ascontiguousarray(state, dtype=np.uint8)
+        if s.shape != self.shape:
+            raise ValueError(f"state must be {self.shape}, got {s.shape}")
+        self._check(self._lib.fhp_set_state(self._h, _ptr(s)))
+
+    def get_state(self) -> np.ndarray:
+        out = np.empty(self.shape, dtype=np.uint8)
+        self._check(self._lib.fhp_get_state(self._h, _ptr(out)))
+        return out
+
+    def set_state_tensor(self, t):
+        torch = _torch()
+        if t.dtype != torch.uint8 or tuple(t.shape) != self.shape or not t.is_contiguous() \
+                or t.device != self.device:
+            raise ValueError("expected a contiguous uint8 tensor of shape (H, W) on the lattice's device")
+        self._check(self._lib.fhp_set_state_device(self._h, ctypes.c_void_p(t.data_ptr())))
+
+    def get_state_tensor(self, out=None):
+        torch = _torch()
+        if out is None:
+            out = torch.empty(self.shape, dtype=torch.uint8, device=self.device)
+        self._check(self._lib.fhp_get_state_device(self._h, ctypes.c_void_p(out.data_ptr())))
+        return out
+
+    def load_obstacles(self, mask: np.ndarray):
+        m = np.ascontiguousarray(mask).astype(np.uint8, copy=False)
+        if m.shape != self.shape:
+            raise ValueError(f"mask must be {self.shape}")
+        self._check(self._lib.fhp_load_obstacles(self._h, _ptr(m)))
+
+    # -- dynamics -------------------------------------------------------------
+    def step(self, n: int = 1):
+        self._check(self._lib.fhp_step(self._h, int(n)))
+
+    @property
+    def t(self) -> int:
+        return int(self._lib.fhp_get_time(self._h))
+
+    def set_time(self, t: int):
+        self._check(self._lib.fhp_set_time(self._h, int(t)))
+
+    def set_forcing(self, p: float):
+        self._check(self._lib.fhp_set_forcing(self._h, float(p)))
+        self.forcing_p = float(p)
+
+    def set_temporal_block(self, k: int):
+        self._check(self._lib.fhp_set_temporal_block(self._h, int(k)))
+
+    def synchronize(self):
+        self._check(self._lib.fhp_synchronize(self._h))
+
+    @property
+    def kernel_launches(self) -> int:
+        return int(self._lib.fhp_kernel_launches(self._h))
+
+    # -- observables ----------------------------------------------------------
+    def coarse_grain(self, block: int = 32):
+        nby, nbx = self.height // block, self.width // block
+        counts = np.empty((nby, nbx, 9), dtype=np.int32)
+        rho = np.empty((nby, nbx), dtype=np.float32)
+        ux = np.empty_like(rho)
+        uy = np.empty_like(rho)
+        self._check(self._lib.fhp_coarse_grain(self._h, int(block), _ptr(counts), _ptr(rho),
+                                               _ptr(ux), _ptr(uy)))
+        return counts, rho, ux, uy
+
+    def coarse_grain_into(self, block: int, counts, rho, ux, uy):
+        """Coarse-grain into preallocated device tensors (asynchronous)."""
+        self._check(self._lib.fhp_coarse_grain_device(
+            self._h, int(block), ctypes.c_void_p(counts.data_ptr()), ctypes.c_void_p(rho.data_ptr()),
+            ctypes.c_void_p(ux.data_ptr()), ctypes.c_void_p(uy.data_ptr())))
+
+    def coarse_grain_host_into(self, block: int, counts: np.ndarray, rho: np.ndarray,
+                               ux: np.ndarray, uy: np.ndarray):
+        """Coarse-grain into preallocated host arrays (synchronous)."""
+        self._check(self._lib.fhp_coarse_grain(self._h, int(block), _ptr(counts), _ptr(rho),
+                                               _ptr(ux), _ptr(uy)))
+
+    def coarse_grain_tensor(self, block: int = 32):
+        torch = _torch()
+        nby, nbx = self.height // block, self.width // block
+        counts = torch.empty((nby, nbx, 9), dtype=torch.int32, device=self.device)
+        rho = torch.empty((nby, nbx), dtype=torch.float32, device=self.device)
+        ux = torch.empty_like(rho)
+        uy = torch.empty_like(rho)
+        self._check(self._lib.fhp_coarse_grain_device(
+            self._h, int(block), ctypes.c_void_p(counts.data_ptr()), ctypes.c_void_p(rho.data_ptr()),
+            ctypes.c_void_p(ux.data_ptr()), ctypes.c_void_p(uy.data_ptr())))
+        return counts, rho, ux, uy
+
+
+def philox4x32_10_device(ctr, key, stream=None):
+    """Philox4x32-10 blocks computed by the library's device code.
+
+    ``ctr``: uint32-valued int64/int32 tensor (n, 4) on the GPU; ``key``: (n, 2)."""
+    torch = _torch()
+    lib = load()
+    c = ctr.to(torch.int32).contiguous()
+    k = key.to(torch.int32).contiguous()
+    out = torch.empty_like(c)
+    s = stream if stream is not None else torch.cuda.current_stream(c.device)
+    rc = lib.fhp_philox4x32_10_device(ctypes.c_void_p(c.data_ptr()), ctypes.c_void_p(k.data_ptr()),
+                                      ctypes.c_void_p(out.data_ptr()), c.shape[0],
+                                      ctypes.c_void_p(s.cuda_stream))
+    if rc != FHP_OK:
+        raise FhpError(rc, lib.fhp_last_error(None).decode())
+    return out

@@ -1,0 +1,48 @@
+"""The C-ABI library builds, loads and exports every function of include/fhp.h.
+
+No compute call is made (these run without a GPU)."""
+import ctypes
+
+import pytest
+
+from paper_1208_2428_gb300 import build as cuda_build
+from paper_1208_2428_gb300 import fhp
+
+
+@pytest.fixture(scope="module")
+def lib():
+    cuda_build.build()
+    return fhp.load()
+
+
+def test_header_declares_the_boundary():
+    names = fhp.exported_names()
+    for required in ("fhp_create", "fhp_load_obstacles", "fhp_step", "fhp_coarse_grain", "fhp_destroy"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    missing = [n for n in fhp.exported_names() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_required_bytes_and_validation_without_gpu(lib):
+    # pure host arithmetic: no CUDA call behind these
+    assert lib.fhp_required_bytes(31, 4) == 0
+    assert lib.fhp_required_bytes(64, 3) == 0
+    assert lib.fhp_required_bytes(32, 0) == 0
+    n = lib.fhp_required_bytes(16384, 4096)
+    planes = 15 * 16384 * 4096 // 8
+    assert planes <= n <= planes + 16384 * 4096 + 4096
+    # ragged rows are padded to whole 16-byte quads
+    assert lib.fhp_required_bytes(96, 2) >= 15 * 2 * 16 + 96 * 2
+    out = ctypes.c_void_p(123)
+    rc = lib.fhp_create(ctypes.byref(out), None)
+    assert rc == fhp.FHP_EINVAL and out.value is None
+    assert b"params" in lib.fhp_last_error(None)
+    p = fhp._Params(100, 4, 0, 0.0, None, None, 0)
+    assert lib.fhp_create(ctypes.byref(out), ctypes.byref(p)) == fhp.FHP_EINVAL
+    p = fhp._Params(64, 4, 0, 1.5, None, None, 0)
+    assert lib.fhp_create(ctypes.byref(out), ctypes.byref(p)) == fhp.FHP_EINVAL
+    assert lib.fhp_step(None, 1) == fhp.FHP_EINVAL
+    lib.fhp_destroy(None)

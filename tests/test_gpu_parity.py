@@ -1,0 +1,224 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle.
+
+Lattice states and integer coarse-grained counts must be bit-exact; derived
+float fields within 1e-6 relative (they are computed in double on both sides
+and rounded to float, so they usually agree exactly)."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+FLOAT_RTOL = 1e-6
+
+
+@pytest.fixture(scope="module")
+def fhp_mod():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1208_2428_gb300 import build as cuda_build
+    cuda_build.build()
+    import paper_1208_2428_gb300 as pkg
+    pkg.load()
+    return pkg
+
+
+def gpu_run(pkg, s0, seed, t0, n, p, chunks=None):
+    H, W = s0.shape
+    with pkg.Lattice(W, H, seed=seed, forcing_p=p) as lat:
+        lat.set_state(s0)
+        lat.set_time(t0)
+        for c in (chunks or [n]):
+            lat.step(c)
+        assert lat.t == t0 + n
+        return lat.get_state()
+
+
+def assert_same(got, want, what=""):
+    if not np.array_equal(got, want):
+        diff = np.argwhere(got != want)
+        y, x = diff[0]
+        raise AssertionError(f"{what}: {len(diff)} nodes differ; first at (x={x}, y={y}): "
+                             f"gpu {got[y, x]:08b} oracle {want[y, x]:08b}")
+
+
+def test_roundtrip_bytes(fhp_mod):
+    rng = np.random.Generator(np.random.PCG64(5))
+    for W, H in [(32, 2), (96, 6), (160, 4), (4128, 4), (256, 256)]:
+        s = rng.integers(0, 256, size=(H, W), dtype=np.uint8)  # includes particles on solid nodes
+        with fhp_mod.Lattice(W, H, seed=1) as lat:
+            lat.set_state(s)
+            assert_same(lat.get_state(), s, f"roundtrip {W}x{H}")
+            lat.step(0)
+            assert_same(lat.get_state(), s, "step(0)")
+
+
+SHAPES = [
+    (32, 2), (32, 4), (64, 2), (96, 6), (128, 8), (160, 4), (192, 10), (224, 6), (256, 12),
+    (384, 4), (480, 6), (992, 8),          # narrow rows: several rows of one parity per warp
+    (4096, 4), (4128, 4), (4160, 6), (4192, 2), (8192 + 96, 4), (12288, 2),  # wide rows, ragged tails
+]
+
+
+@pytest.mark.parametrize("W,H", SHAPES)
+@pytest.mark.parametrize("variant", ["periodic", "walls_forcing", "points_forcing"])
+def test_parity_shapes(fhp_mod, oracle_mod, W, H, variant):
+    seed = 1000 + W + 7 * H
+    rng = np.random.Generator(np.random.PCG64(seed))
+    if variant == "periodic":
+        solid, p = None, 0.0
+    elif variant == "walls_forcing":
+        solid, p = workloads.channel_walls(W, H), 0.05
+    else:
+        solid, p = workloads.random_points(W, H, 0.05, rng), 0.2
+    s0 = workloads.bernoulli_lattice(W, H, 0.35, seed, solid)
+    steps = 9
+    want, _ = oracle_mod.run(s0, seed, 3, steps, p)
+    got = gpu_run(fhp_mod, s0, seed, 3, steps, p)
+    assert_same(got, want, f"{W}x{H} {variant}")
+
+
+def test_parity_empty_and_full(fhp_mod, oracle_mod):
+    for W, H in [(64, 4), (4160, 2)]:
+        for fill in (0x00, 0x7F, 0x3F, 0x40):
+            s0 = np.full((H, W), fill, dtype=np.uint8)
+            want, _ = oracle_mod.run(s0, 3, 0, 5, 0.5)
+            got = gpu_run(fhp_mod, s0, 3, 0, 5, 0.5)
+            assert_same(got, want, f"fill {fill:#x}")
+        s0 = np.full((H, W), 0xFF, dtype=np.uint8)   # all solid, full of particles
+        want, _ = oracle_mod.run(s0, 3, 0, 4, 0.5)
+        assert_same(gpu_run(fhp_mod, s0, 3, 0, 4, 0.5), want, "all solid")
+
+
+def test_parity_large_step_counter(fhp_mod, oracle_mod):
+    """Counters above 2^32 use the high half of t in the random streams."""
+    W, H = 256, 16
+    s0 = workloads.bernoulli_lattice(W, H, 0.3, 9, workloads.channel_walls(W, H))
+    t0 = (7 << 32) - 3
+    want, _ = oracle_mod.run(s0, 0xFEDCBA9876543210, t0, 6, 0.1)
+    got = gpu_run(fhp_mod, s0, 0xFEDCBA9876543210, t0, 6, 0.1)
+    assert_same(got, want, "t across 2^32")
+
+
+def test_periodic_256_full(fhp_mod, oracle_mod):
+    """256 x 256 periodic, density 0.3, seed 1, 100 steps: final state and
+    per-direction totals bit-exact."""
+    job = workloads.periodic_256()
+    s0 = job.initial_state()
+    want, _ = oracle_mod.run(s0, job.seed, 0, job.steps, job.p)
+    got = gpu_run(fhp_mod, s0, job.seed, 0, job.steps, job.p, chunks=[1, 36, 63])
+    assert_same(got, want, "periodic_256")
+    for k in range(7):
+        assert int(np.count_nonzero(got >> k & 1)) == int(np.count_nonzero(want >> k & 1))
+
+
+def test_channel_coarse_grain(fhp_mod, oracle_mod):
+    """4096 x 1024 channel (walls, p = 1e-3): state and 32 x 32 coarse-grained
+    fields after 1,000 steps (the first output time of the run)."""
+    job = workloads.channel_4096x1024()
+    s0 = job.initial_state()
+    n = 1000
+    want, ev = oracle_mod.run(s0, job.seed, 0, n, job.p)
+    assert ev > 0
+    with fhp_mod.Lattice(job.W, job.H, seed=job.seed, forcing_p=job.p) as lat:
+        lat.set_state(s0)
+        lat.step(n)
+        got = lat.get_state()
+        counts, rho, ux, uy = lat.coarse_grain(32)
+        d_counts, d_rho, d_ux, d_uy = lat.coarse_grain_tensor(32)
+    assert_same(got, want, "channel")
+    c_ref, rho_ref, ux_ref, uy_ref = oracle_mod.coarse_grain(want, 32)
+    assert np.array_equal(counts, c_ref)
+    assert np.array_equal(d_counts.cpu().numpy(), c_ref)
+    for g, r in ((rho, rho_ref), (ux, ux_ref), (uy, uy_ref)):
+        np.testing.assert_allclose(g, r.astype(np.float32), rtol=FLOAT_RTOL, atol=1e-30)
+    np.testing.assert_array_equal(d_rho.cpu().numpy(), rho)
+    # physics sanity (qualitative): forcing drives a mean flow toward +x
+    assert float(ux[1:-1].mean()) > 0
+
+
+def test_cylinder_full_size(fhp_mod, oracle_mod):
+    """16384 x 4096 cylinder workload at full size in the benchmark's launch
+    configuration: whole state bit-exact after 12 steps."""
+    job = workloads.cylinder_16384x4096()
+    s0 = job.initial_state()
+    n = 12
+    want, ev = oracle_mod.run(s0, job.seed, 0, n, job.p)
+    got = gpu_run(fhp_mod, s0, job.seed, 0, n, job.p)
+    assert_same(got, want, "cylinder 16384x4096")
+
+
+def test_resume_from_checkpoint(fhp_mod):
+    W, H = 4160, 6
+    s0 = workloads.bernoulli_lattice(W, H, 0.3, 21, workloads.channel_walls(W, H))
+    full = gpu_run(fhp_mod, s0, 21, 0, 30, 0.05)
+    with fhp_mod.Lattice(W, H, seed=21, forcing_p=0.05) as a:
+        a.set_state(s0)
+        a.step(13)
+        ckpt, t = a.get_state(), a.t
+    with fhp_mod.Lattice(W, H, seed=21, forcing_p=0.05) as b:
+        b.set_state(ckpt)
+        b.set_time(t)
+        b.step(17)
+        assert_same(b.get_state(), full, "resume")
+
+
+def test_load_obstacles_clears_particles(fhp_mod, oracle_mod):
+    W, H = 256, 32
+    s0 = workloads.bernoulli_lattice(W, H, 0.4, 4)
+    mask = workloads.cylinder_mask(W, H)
+    with fhp_mod.Lattice(W, H, seed=4, forcing_p=0.01) as lat:
+        lat.set_state(s0)
+        lat.load_obstacles(mask)
+        after = lat.get_state()
+        expect = np.where(mask, 0x80, s0).astype(np.uint8)
+        assert_same(after, expect, "load_obstacles")
+        lat.step(7)
+        got = lat.get_state()
+    want, _ = oracle_mod.run(expect, 4, 0, 7, 0.01)
+    assert_same(got, want, "after obstacles")
+
+
+def test_device_state_io(fhp_mod, oracle_mod):
+    import torch
+    W, H = 4128, 4
+    s0 = workloads.bernoulli_lattice(W, H, 0.3, 8, workloads.channel_walls(W, H))
+    with fhp_mod.Lattice(W, H, seed=8, forcing_p=0.02) as lat:
+        lat.set_state_tensor(torch.from_numpy(s0).cuda())
+        lat.step(5)
+        got = lat.get_state_tensor().cpu().numpy()
+    want, _ = oracle_mod.run(s0, 8, 0, 5, 0.02)
+    assert_same(got, want, "device io")
+
+
+def test_errors(fhp_mod):
+    with pytest.raises(fhp_mod.FhpError):
+        fhp_mod.Lattice(48, 4)
+    with pytest.raises(fhp_mod.FhpError):
+        fhp_mod.Lattice(64, 5)
+    with fhp_mod.Lattice(64, 64) as lat:
+        with pytest.raises(fhp_mod.FhpError):
+            lat.coarse_grain(48)
+        with pytest.raises(fhp_mod.FhpError):
+            lat.step(-1)
+        with pytest.raises(fhp_mod.FhpError):
+            lat.set_forcing(2.0)
+        with pytest.raises(fhp_mod.FhpError):
+            lat.set_time(1 << 48)
+
+
+def test_device_philox_matches_oracle(fhp_mod, oracle_mod):
+    import torch
+    rng = np.random.Generator(np.random.PCG64(77))
+    n = 200_000
+    ctr = rng.integers(0, 2**32, size=(n, 4), dtype=np.uint64).astype(np.uint32)
+    key = rng.integers(0, 2**32, size=(n, 2), dtype=np.uint64).astype(np.uint32)
+    out = fhp_mod.philox4x32_10_device(torch.from_numpy(ctr.view(np.int32)).cuda(),
+                                       torch.from_numpy(key.view(np.int32)).cuda())
+    got = out.cpu().numpy().view(np.uint32)
+    for i in list(range(0, n, 997)) + [n - 1]:
+        assert np.array_equal(got[i], oracle_mod.philox4x32_10(ctr[i], key[i])), i
