@@ -81,8 +81,9 @@ FHP_API int fhp_create(fhp_lattice** out, const fhp_params* params);
  * queued on the lattice's stream.  NULL is accepted and ignored. */
 FHP_API void fhp_destroy(fhp_lattice* lattice);
 
-/* Message for the last failed call on `lattice`, or of the calling thread's
- * last failed fhp_create when `lattice` is NULL.  Never NULL; "" if none. */
+/* Message for the last failed call on `lattice`, or, when `lattice` is NULL,
+ * of the calling thread's last failed call that takes no lattice
+ * (fhp_create, fhp_run_static, fhp_philox4x32_10_device).  Never NULL. */
 FHP_API const char* fhp_last_error(const fhp_lattice* lattice);
 
 /* Replace the whole lattice state, solid flags included (bit 7), from H x W
@@ -157,6 +158,42 @@ FHP_API int64_t fhp_kernel_launches(const fhp_lattice* lattice);
  * Asynchronous on `stream` (cudaStream_t, NULL = legacy default stream). */
 FHP_API int fhp_philox4x32_10_device(const uint32_t* device_ctr, const uint32_t* device_key,
                              uint32_t* device_out, int64_t n, void* stream);
+
+/* Size in bytes of the device array that fhp_run_static works in. */
+#define FHP_STATIC_SCRATCH_BYTES (16u << 20)
+
+/* fhp_run_static: advance a lattice by n steps without allocating any device
+ * memory.  This entry point has no counterpart in the paper; it exists for
+ * callers that cannot allocate device memory -- plugins whose host
+ * application owns all GPU memory through its own pool, services with a hard
+ * device-memory cap fixed at start-up, and latency-critical loops where an
+ * allocation, which may synchronise the device, is not acceptable.
+ *
+ * device_bytes_in / device_bytes_out: H x W node bytes (same layout as
+ * fhp_set_state, solid flags in bit 7) in device memory of the current
+ * device, owned by the caller; they may be the same buffer.  The run starts
+ * at step t0 with the generator key `seed` and forcing probability
+ * `forcing_p`, and gives exactly the state that fhp_create + fhp_set_state +
+ * fhp_set_time(t0) + fhp_step(n) + fhp_get_state would give.  Asynchronous
+ * on `stream` (cudaStream_t, NULL = legacy default stream).
+ *
+ * All intermediate data (two bit-plane state buffers, the solid plane, a flag
+ * word) live in one file-scope __device__ array of FHP_STATIC_SCRATCH_BYTES
+ * bytes, which every GPU that loads the library holds until the process
+ * exits.  The call calls no cudaMalloc, cudaFree or other allocating routine.
+ * Limit: 15 bit-planes of the lattice (rows padded to 128 nodes) plus 256
+ * bytes must fit, i.e. up to about 8.9 million nodes (4096 x 2048 fits,
+ * 4096 x 4096 does not); larger lattices fail with FHP_EINVAL.
+ * The first call on a device looks the array's device address up
+ * (cudaGetSymbolAddress, with that device current); make that first call
+ * before any stream capture.  Every call on a device shares the array and it
+ * keeps the previous call's contents (the call rewrites all of it that it
+ * reads, and clears the flag word); calls whose GPU work overlaps -- from
+ * different streams or host threads -- race on it and must be serialised by
+ * the caller.  On failure fhp_last_error(NULL) describes the error. */
+FHP_API int fhp_run_static(const uint8_t* device_bytes_in, uint8_t* device_bytes_out, int32_t width,
+                           int32_t height, uint64_t seed, int64_t t0, int64_t n, double forcing_p,
+                           void* stream);
 
 #ifdef __cplusplus
 }

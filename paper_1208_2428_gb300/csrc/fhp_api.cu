@@ -130,6 +130,8 @@ int read_solid_flag(fhp_lattice* h) {
 
 }  // namespace
 
+void fhp::set_thread_error(const char* message) { g_create_error = message; }
+
 extern "C" {
 
 size_t fhp_required_bytes(int32_t width, int32_t height) {

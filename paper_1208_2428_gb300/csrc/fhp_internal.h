@@ -74,6 +74,9 @@ cudaError_t launch_coarse_grain(const Geometry& g, const uint32_t* state, const 
                                 bool has_solid, int B, int32_t* counts, float* rho, float* ux,
                                 float* uy, cudaStream_t stream);
 
+// Record the calling thread's last error (returned by fhp_last_error(NULL)).
+void set_thread_error(const char* message);
+
 // Philox4x32-10 over n counters (diagnostic entry point).
 cudaError_t launch_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, int64_t n,
                           cudaStream_t stream);
