@@ -49,6 +49,7 @@ def parse_args():
     ap.add_argument("--lattice-steps", type=int, default=None,
                     help="time steps per benchmark step (default: the workload's run length)")
     ap.add_argument("--temporal-block", type=int, default=1)
+    ap.add_argument("--step-kernel", type=int, default=0, help="0 auto, 1 direct, 2 bulk-copy ring")
     ap.add_argument("--cg-block", type=int, default=32)
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="target CPU time of the oracle baseline sample")
@@ -245,7 +246,7 @@ def run_gpu(args):
 
     job = workload(args.workload)
     nsteps = args.lattice_steps or job.steps
-    B = args.cg_block
+    B = args.cg_block if (job.W % args.cg_block == 0 and job.H % args.cg_block == 0) else 0
     s0 = job.initial_state()
     seed = job.seed + 1_000_003 * rank   # independent replicas per rank
     has_solid = bool((s0 & 0x80).any())
@@ -254,16 +255,21 @@ def run_gpu(args):
     lat = Lattice(job.W, job.H, seed=seed, forcing_p=job.p, device=dev, stream=stream)
     lat.set_state(s0)
     lat.set_temporal_block(args.temporal_block)
-    nby, nbx = job.H // B, job.W // B
+    lat.set_step_kernel(args.step_kernel)
+    nby, nbx = (job.H // B, job.W // B) if B else (1, 1)
     counts = torch.empty((nby, nbx, 9), dtype=torch.int32, device=dev)
     rho = torch.empty((nby, nbx), dtype=torch.float32, device=dev)
     ux = torch.empty_like(rho)
     uy = torch.empty_like(rho)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
 
+    def coarse():
+        if B:
+            lat.coarse_grain_into(B, counts, rho, ux, uy)
+
     def bench_step():
         lat.step(nsteps)
-        lat.coarse_grain_into(B, counts, rho, ux, uy)
+        coarse()
 
     for _ in range(args.warmup):
         bench_step()
@@ -286,13 +292,14 @@ def run_gpu(args):
         starts[i].record(stream)
         lat.step(nsteps)
         mids[i].record(stream)
-        lat.coarse_grain_into(B, counts, rho, ux, uy)
+        coarse()
         ends[i].record(stream)
     torch.cuda.synchronize(dev)
     if dist:
         dist.barrier()
     launches = lat.kernel_launches - launches0
     clocks = sampler.stop()
+    kernel_name = {1: "fhp_step_direct_kernel", 2: "fhp_step_tma_kernel"}.get(lat.step_kernel, "?")
     total_ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
     step_kernel_ms = sum(s.elapsed_time(m) for s, m in zip(starts, mids))
     if dist:
@@ -318,17 +325,20 @@ def run_gpu(args):
         h_ux = np.empty_like(h_rho)
         h_uy = np.empty_like(h_rho)
         e2e_steps = max(3, min(args.steps, 10))
-        lat.set_state(host_state)
-        lat.step(nsteps)
-        lat.coarse_grain_host_into(B, h_counts, h_rho, h_ux, h_uy)
+        def e2e_step():
+            lat.set_state(host_state)
+            lat.step(nsteps)
+            if B:
+                lat.coarse_grain_host_into(B, h_counts, h_rho, h_ux, h_uy)
+            else:
+                lat.synchronize()
+        e2e_step()
         if dist:
             dist.barrier()
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
         for _ in range(e2e_steps):
-            lat.set_state(host_state)
-            lat.step(nsteps)
-            lat.coarse_grain_host_into(B, h_counts, h_rho, h_ux, h_uy)
+            e2e_step()
         torch.cuda.synchronize(dev)
         e2e_s = time.perf_counter() - t0
         if dist:
@@ -337,7 +347,7 @@ def run_gpu(args):
             e2e_s = float(t[0])
         e2e = {"value": world * nodes * nsteps * e2e_steps / e2e_s / 1e9, "unit": UNIT,
                "h2d_bytes_per_step": int(s0.nbytes),
-               "d2h_bytes_per_step": int(h_counts.nbytes + h_rho.nbytes + h_ux.nbytes + h_uy.nbytes),
+               "d2h_bytes_per_step": int(h_counts.nbytes + h_rho.nbytes + h_ux.nbytes + h_uy.nbytes) if B else 0,
                "steps": e2e_steps}
 
     cpu = None
@@ -353,12 +363,13 @@ def run_gpu(args):
             "config": {"workload": job.name, "W": job.W, "H": job.H, "lattice_steps_per_step": nsteps,
                        "coarse_grain_block": B, "forcing_p": job.p, "density": job.density,
                        "seed": job.seed, "temporal_block": args.temporal_block,
+                       "step_kernel": kernel_name,
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                        "l2": "flushed (512 MB write) before every timed step; the 120 MB working "
                              "set is below the 126 MB L2 within a step"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
-                         "kernel": "fhp_step_kernel", "algorithmic_bytes_per_node": bytes_per_node,
+                         "kernel": kernel_name, "algorithmic_bytes_per_node": bytes_per_node,
                          "peak_source": peak_src,
                          "launch_us": launch_s * 1e6},
             "cpu_baseline": cpu,

@@ -145,8 +145,21 @@ FHP_API int fhp_set_forcing(fhp_lattice* lattice, double p);
  * or 8.  Results are identical for every value.  Default 1. */
 FHP_API int fhp_set_temporal_block(fhp_lattice* lattice, int32_t k);
 
+/* Step kernel used by fhp_step: 0 = automatic (default), 1 = direct (one
+ * 128-node quad per thread, operands loaded into registers), 2 = bulk-copy
+ * ring (persistent CTAs stage tiles of full rows in shared memory with
+ * cp.async.bulk; falls back to 1 when a row does not fit a stage).  Results
+ * are identical for every choice. */
+FHP_API int fhp_set_step_kernel(fhp_lattice* lattice, int32_t kind);
+
+/* The step kernel fhp_step will run for the lattice's current settings
+ * (1 or 2), or -1 for a NULL lattice. */
+FHP_API int fhp_get_step_kernel(const fhp_lattice* lattice);
+
 /* Block the calling thread until all work queued on the lattice's stream
- * has finished; reports asynchronous CUDA errors. */
+ * has finished; reports asynchronous CUDA errors, and FHP_ETIMEOUT if a step
+ * kernel gave up waiting for its input copies (the state is then
+ * unreliable). */
 FHP_API int fhp_synchronize(fhp_lattice* lattice);
 
 /* Number of kernel launches this lattice has issued since creation. */

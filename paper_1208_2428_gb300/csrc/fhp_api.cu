@@ -28,13 +28,14 @@ struct fhp_lattice {
     size_t bytes = 0;
     uint32_t* buf[2] = {nullptr, nullptr};
     uint32_t* solid = nullptr;
-    unsigned int* flags = nullptr;  // device word: any solid node
+    unsigned int* flags = nullptr;  // device words: [0] any solid node, [1] kernel wait gave up
     uint8_t* staging = nullptr;
     size_t staging_bytes = 0;
     int cur = 0;
     int64_t t = 0;
     bool has_solid = false;
     int k_block = 1;
+    int step_kernel = fhp::kStepAuto;
     int64_t launches = 0;
     std::string err;
 };
@@ -119,13 +120,28 @@ int check_block(fhp_lattice* h, int32_t B) {
     return FHP_OK;
 }
 
+// Device-side error word: a bounded wait in a kernel gave up.  Reads it after
+// the stream has drained, clears it, and reports FHP_ETIMEOUT if it was set.
+int check_device_error(fhp_lattice* h) {
+    unsigned int word = 0;
+    cudaError_t e = cudaMemcpyAsync(&word, h->flags + 1, sizeof word, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "reading the device error word");
+    if (word) {
+        cudaMemsetAsync(h->flags + 1, 0, sizeof word, h->stream);
+        cudaStreamSynchronize(h->stream);
+        return fail(h, FHP_ETIMEOUT, "a step kernel gave up waiting for its input copies; the state is unreliable");
+    }
+    return FHP_OK;
+}
+
 int read_solid_flag(fhp_lattice* h) {
     unsigned int flag = 0;
     cudaError_t e = cudaMemcpyAsync(&flag, h->flags, sizeof flag, cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "reading the solid flag");
     h->has_solid = flag != 0;
-    return FHP_OK;
+    return check_device_error(h);
 }
 
 }  // namespace
@@ -242,7 +258,7 @@ int fhp_get_state(fhp_lattice* h, uint8_t* host_bytes) {
     cudaError_t e = cudaMemcpyAsync(host_bytes, h->staging, n, cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "copying the state to the host");
-    return FHP_OK;
+    return check_device_error(h);
 }
 
 int fhp_get_state_device(fhp_lattice* h, uint8_t* device_bytes) {
@@ -277,7 +293,8 @@ int fhp_step(fhp_lattice* h, int64_t n) {
     const fhp::Key2 key{(uint32_t)h->seed, (uint32_t)(h->seed >> 32)};
     for (int64_t i = 0; i < n; ++i) {
         cudaError_t e = fhp::launch_step(h->g, h->buf[h->cur], h->buf[h->cur ^ 1], h->solid, h->has_solid,
-                                         h->force, h->ft, key, (uint64_t)h->t, h->stream);
+                                         h->force, h->ft, key, (uint64_t)h->t, h->stream, h->flags + 1,
+                                         h->step_kernel);
         if (e != cudaSuccess) return cuda_fail(h, e, "launching the step kernel");
         ++h->launches;
         h->cur ^= 1;
@@ -309,7 +326,7 @@ int fhp_coarse_grain(fhp_lattice* h, int32_t block, int32_t* counts, float* rho,
         e = cudaMemcpyAsync(uy, d_uy, cells * sizeof(float), cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "copying coarse-grained fields to the host");
-    return FHP_OK;
+    return check_device_error(h);
 }
 
 int fhp_coarse_grain_device(fhp_lattice* h, int32_t block, int32_t* counts, float* rho, float* ux, float* uy) {
@@ -350,12 +367,25 @@ int fhp_set_temporal_block(fhp_lattice* h, int32_t k) {
     return FHP_OK;
 }
 
+int fhp_set_step_kernel(fhp_lattice* h, int32_t kind) {
+    if (!h) return fail(nullptr, FHP_EINVAL, "lattice is NULL");
+    if (kind < 0 || kind > 2) return fail(h, FHP_EINVAL, "step kernel %d not in {0, 1, 2}", kind);
+    h->step_kernel = kind;
+    return FHP_OK;
+}
+
+int fhp_get_step_kernel(const fhp_lattice* h) {
+    if (!h) return -1;
+    DeviceGuard dg(h->device);
+    return fhp::resolved_step_kernel(h->g, h->has_solid, h->step_kernel);
+}
+
 int fhp_synchronize(fhp_lattice* h) {
     if (!h) return fail(nullptr, FHP_EINVAL, "lattice is NULL");
     DeviceGuard dg(h->device);
     cudaError_t e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "synchronizing");
-    return FHP_OK;
+    return check_device_error(h);
 }
 
 int64_t fhp_kernel_launches(const fhp_lattice* h) { return h ? h->launches : -1; }

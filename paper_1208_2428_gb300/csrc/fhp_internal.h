@@ -46,13 +46,32 @@ struct StepArgs {
     int warps_per_row;       // nq >= 32: warps covering one row
     Key2 key;
     uint32_t t_lo, t_hi;
+    unsigned int* err;       // set nonzero if a bounded device-side wait gives up
     ForcingTable ft;
 };
 
+// Row tiling of the bulk-copy step kernel: tiles of R full rows, staged in a
+// ring of shared-memory buffers by cp.async.bulk.
+struct TileArgs {
+    int R;                         // rows per tile
+    int ntiles;                    // ceil(H / R)
+    unsigned long long nq_magic;   // ceil(2^32 / nq): j / nq == (j * nq_magic) >> 32 for small j
+};
+
+// Step kernel choice: automatic, direct register loads, or the bulk-copy ring
+// (cp.async.bulk into shared memory; falls back to direct when a row does not
+// fit a stage).  Automatic picks the ring when it gets >= 2 tiles per SM.
+enum StepKernel { kStepAuto = 0, kStepDirect = 1, kStepRing = 2 };
+
 // Launch one time step (motion, scattering, bounce-back, forcing).
+// `err` (device word, may be NULL) is set nonzero if a bounded wait gives up.
 cudaError_t launch_step(const Geometry& g, const uint32_t* src, uint32_t* dst,
                         const uint32_t* solid, bool has_solid, bool force,
-                        const ForcingTable& ft, Key2 key, uint64_t t, cudaStream_t stream);
+                        const ForcingTable& ft, Key2 key, uint64_t t, cudaStream_t stream,
+                        unsigned int* err = nullptr, int kernel = kStepAuto);
+
+// The kernel launch_step(kernel = requested) runs: kStepDirect or kStepRing.
+int resolved_step_kernel(const Geometry& g, bool has_solid, int requested);
 
 // Pack H x W node bytes (device) into 7 state planes + the solid plane.
 // Sets *device_any_solid to a nonzero value if any node is solid.

@@ -1,22 +1,32 @@
-// fhp_step.cu -- one fused FHP time step on bit-planes (k = 1).
+// fhp_step.cu -- one fused FHP time step on bit-planes.
 //
-// One thread owns one quad (4 consecutive words = 128 nodes) of one row y and
-// writes S_{t+1} for it:
+// The unit of work is a quad: 4 consecutive words (128 nodes) of one row y.
+// For each quad the step computes S_{t+1}:
 //   motion (arXiv:1208.2428 Section 2, Fig. 3): the particle moving along c_i
-//     that arrives at (x, y) left (x, y) - c_i; rows y-1, y, y+1 each feed the
-//     directions that point away from them, and the half-cell shift of odd
-//     rows decides, per direction, whether the source sits one node to the
-//     left, at the same x, or one node to the right;
-//   the one-node shifts are funnel shifts across the words of the quad; the
-//     word beyond the quad comes from the neighbouring lane (__shfl_sync) or,
-//     at a warp or row edge, from a global load (periodic wrap in x);
-//   scattering with bounce-back and forcing (device functions of
-//     fhp_device.cuh); one Philox block gives the chirality bits of the
-//     quad's 128 nodes, a second one its forcing draws;
-//   128-bit loads and stores of the seven planes (two ping-pong buffers).
-// The row parity is uniform within a warp: wide rows (>= 32 quads) give each
-// warp 32 quads of one row; narrow rows pack whole rows of one parity into a
-// warp.
+//     that arrives at (x, y) left (x, y) - c_i; row y-1 feeds the upward
+//     movers (NE 3, NW 4), row y the horizontal movers (E 2, W 5) and the rest
+//     particle, row y+1 the downward movers (SW 0, SE 1); the half-cell shift
+//     of odd rows decides, per direction, whether the source sits one node to
+//     the left, at the same x, or one node to the right.  One-node shifts are
+//     funnel shifts across the quad's words plus one neighbour word (periodic
+//     wrap in x);
+//   scattering with bounce-back and forcing (fhp_device.cuh); one Philox
+//     block gives the chirality bits of the quad's 128 nodes, a second one its
+//     first forcing draws;
+//   128-bit stores of the seven planes into the other ping-pong buffer.
+//
+// Two kernels share that per-quad code:
+//   fhp_step_tma_kernel    persistent CTAs walk tiles of R full rows; one
+//                          thread streams each tile's plane rows into a
+//                          3-stage shared-memory ring with cp.async.bulk
+//                          (completion on an mbarrier), so loads for the next
+//                          tiles are in flight while all threads compute;
+//   fhp_step_direct_kernel one quad per thread, operands loaded straight into
+//                          registers and neighbour words exchanged with
+//                          __shfl_sync (used when a row is too wide to stage).
+#include <cstdio>
+#include <mutex>
+
 #include "fhp_device.cuh"
 #include "fhp_internal.h"
 
@@ -24,12 +34,285 @@ namespace fhp {
 namespace {
 
 constexpr unsigned kFull = 0xFFFFFFFFu;
-constexpr int kBlock = 256;
+constexpr int kBlock = 256;             // direct kernel
+constexpr int kTmaThreads = 256;        // bulk-copy kernel
+constexpr int kStages = 3;              // shared-memory ring depth
+constexpr int kStageBudget = 32 * 1024; // bytes per stage
+constexpr int kBarrierBytes = 128;      // mbarriers at the front of shared memory
+constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // 2 s bound on any wait
 
+__device__ __forceinline__ uint4 ld4(const uint32_t* p) { return *reinterpret_cast<const uint4*>(p); }
+__device__ __forceinline__ void st4(uint32_t* p, uint4 v) { *reinterpret_cast<uint4*>(p) = v; }
+
+// New bit x takes old bit x-1; `left` is the word left of the quad.
+__device__ __forceinline__ uint4 pull_left(uint4 v, uint32_t left) {
+    return make_uint4(__funnelshift_l(left, v.x, 1), __funnelshift_l(v.x, v.y, 1),
+                      __funnelshift_l(v.y, v.z, 1), __funnelshift_l(v.z, v.w, 1));
+}
+
+// New bit x takes old bit x+1; `right` is the word right of the quad's last
+// valid word (m valid words; the rest of a ragged last quad is padding).
+template <bool RAGGED>
+__device__ __forceinline__ uint4 pull_right(uint4 v, uint32_t right, int m) {
+    uint32_t n0 = v.y, n1 = v.z, n2 = v.w;
+    if (RAGGED) {
+        if (m == 1) n0 = right;
+        if (m == 2) n1 = right;
+        if (m == 3) n2 = right;
+    }
+    return make_uint4(__funnelshift_r(v.x, n0, 1), __funnelshift_r(v.y, n1, 1),
+                      __funnelshift_r(v.z, n2, 1), __funnelshift_r(v.w, right, 1));
+}
+
+// Scattering, bounce-back, forcing and the store of one quad whose movers
+// have already been pulled (n0..n5), with rest plane i6 and solid plane sd.
+template <bool SOLID, bool FORCE, bool RAGGED>
+__device__ __forceinline__ void finish_quad(const StepArgs& a, int q, int y, int m, uint4 n0, uint4 n1,
+                                            uint4 n2, uint4 n3, uint4 n4, uint4 n5, uint4 i6,
+                                            uint4 sd, bool active) {
+    const uint4 chi = rng_block((uint32_t)q, (uint32_t)y, a.t_lo, a.t_hi, 0u, a.key);
+    uint4 gate = make_uint4(0u, 0u, 0u, 0u);
+    if (FORCE) gate = rng_block((uint32_t)q, (uint32_t)y, a.t_lo, a.t_hi, 1u, a.key);
+
+    uint4 o0, o1, o2, o3, o4, o5, o6;
+#define FHP_WORD(J, C)                                                                          \
+    {                                                                                           \
+        Planes7 in{n0.C, n1.C, n2.C, n3.C, n4.C, n5.C, i6.C};                                   \
+        Planes7 out = scatter(in, SOLID ? sd.C : 0u, chi.C);                                    \
+        if (FORCE) {                                                                            \
+            const uint32_t cand = (SOLID ? ~sd.C : 0xFFFFFFFFu) & out.m5 & ~out.m2;             \
+            const uint32_t u = gate.C;                                                          \
+            if (cand != 0u && (unsigned long long)u < a.ft.q[32]) {                             \
+                const uint32_t f = forced_mask(cand, u, a.ft, [&](uint32_t d) {                 \
+                    return word_of(rng_block((uint32_t)q, (uint32_t)y, a.t_lo, a.t_hi, 1u + d,   \
+                                             a.key), J);                                        \
+                });                                                                             \
+                out.m5 ^= f;                                                                    \
+                out.m2 ^= f;                                                                    \
+            }                                                                                   \
+        }                                                                                       \
+        o0.C = out.m0; o1.C = out.m1; o2.C = out.m2; o3.C = out.m3;                             \
+        o4.C = out.m4; o5.C = out.m5; o6.C = out.rest;                                          \
+    }
+    FHP_WORD(0, x)
+    FHP_WORD(1, y)
+    FHP_WORD(2, z)
+    FHP_WORD(3, w)
+#undef FHP_WORD
+
+    if (!active) return;
+    if (RAGGED && m < 4) {
+        // Keep the padding words of the last quad zero.
+        if (m < 2) { o0.y = o1.y = o2.y = o3.y = o4.y = o5.y = o6.y = 0u; }
+        if (m < 3) { o0.z = o1.z = o2.z = o3.z = o4.z = o5.z = o6.z = 0u; }
+        o0.w = o1.w = o2.w = o3.w = o4.w = o5.w = o6.w = 0u;
+    }
+    const size_t pw = a.plane_words;
+    uint32_t* d = a.dst + (size_t)y * a.Pq + 4 * q;
+    st4(d + 0 * pw, o0);
+    st4(d + 1 * pw, o1);
+    st4(d + 2 * pw, o2);
+    st4(d + 3 * pw, o3);
+    st4(d + 4 * pw, o4);
+    st4(d + 5 * pw, o5);
+    st4(d + 6 * pw, o6);
+}
+
+// ---------------------------------------------------------------------------
+// Bulk-copy kernel: mbarrier / cp.async.bulk helpers (inline PTX).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Wait for phase `parity` of `bar`; gives up (returns false) after kWaitLimitNs.
+__device__ __noinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long start = global_ns();
+    for (;;) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (global_ns() - start > kWaitLimitNs) return false;
+    }
+}
+
+__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+
+// Stage layout: slot k (plane k for k < 7, the solid plane for k = 7) holds
+// R rows of Pq words; staged row r of every slot feeds output row y0 + r, so
+// slots 3, 4 hold source rows y0 + r - 1 and slots 0, 1 rows y0 + r + 1.
+template <bool SOLID>
+__device__ void issue_tile(const StepArgs& a, const TileArgs& ta, int tile, uint32_t* stage,
+                           uint64_t* bar) {
+    constexpr int NP = SOLID ? 8 : 7;
+    const int y0 = tile * ta.R;
+    const int rows = min(ta.R, a.H - y0);
+    const uint32_t row_bytes = (uint32_t)a.Pq * 4u;
+    mbar_arrive_expect_tx(bar, (uint32_t)NP * (uint32_t)rows * row_bytes);
+#pragma unroll
+    for (int slot = 0; slot < NP; ++slot) {
+        const uint32_t* plane = slot < 7 ? a.src + (size_t)slot * a.plane_words : a.solid;
+        const int shift = (slot == 3 || slot == 4) ? -1 : (slot == 0 || slot == 1) ? 1 : 0;
+        int r = 0;
+        while (r < rows) {
+            int yy = y0 + shift + r;
+            if (yy < 0) yy += a.H;
+            if (yy >= a.H) yy -= a.H;
+            const int run = min(rows - r, a.H - yy);  // contiguous rows up to the end of the plane
+            bulk_copy_g2s(stage + ((size_t)slot * ta.R + r) * a.Pq, plane + (size_t)yy * a.Pq,
+                          (uint32_t)run * row_bytes, bar);
+            r += run;
+        }
+    }
+}
+
+template <bool SOLID, bool FORCE, bool RAGGED>
+__device__ __forceinline__ void quad_from_stage(const StepArgs& a, const TileArgs& ta, const uint32_t* stage,
+                                                int r, int y, int q) {
+    const int Pq = a.Pq, R = ta.R;
+    const int w = 4 * q;
+    const int m = RAGGED ? (q == a.nq - 1 ? a.Wq - w : 4) : 4;
+    const int wl = q == 0 ? a.Wq - 1 : w - 1;       // word left of the quad (periodic)
+    const int wr = q == a.nq - 1 ? 0 : w + 4;       // word right of the quad (periodic)
+    const uint32_t* s0 = stage + (size_t)r * Pq;    // slot 0, row r
+    const size_t slot = (size_t)R * Pq;
+    const uint4 i0 = ld4(s0 + 0 * slot + w), i1 = ld4(s0 + 1 * slot + w);
+    const uint4 i2 = ld4(s0 + 2 * slot + w), i3 = ld4(s0 + 3 * slot + w);
+    const uint4 i4 = ld4(s0 + 4 * slot + w), i5 = ld4(s0 + 5 * slot + w);
+    const uint4 i6 = ld4(s0 + 6 * slot + w);
+    uint4 sd = make_uint4(0u, 0u, 0u, 0u);
+    if (SOLID) sd = ld4(s0 + 7 * slot + w);
+    uint4 n0, n1, n2, n3, n4, n5;
+    if ((y & 1) == 0) {
+        // Even row: E, NE, SE come from x-1; W from x+1; NW, SW from x.
+        n2 = pull_left(i2, s0[2 * slot + wl]);
+        n3 = pull_left(i3, s0[3 * slot + wl]);
+        n1 = pull_left(i1, s0[1 * slot + wl]);
+        n5 = pull_right<RAGGED>(i5, s0[5 * slot + wr], m);
+        n4 = i4;
+        n0 = i0;
+    } else {
+        // Odd row: E from x-1; W, NW, SW from x+1; NE, SE from x.
+        n2 = pull_left(i2, s0[2 * slot + wl]);
+        n5 = pull_right<RAGGED>(i5, s0[5 * slot + wr], m);
+        n4 = pull_right<RAGGED>(i4, s0[4 * slot + wr], m);
+        n0 = pull_right<RAGGED>(i0, s0[0 * slot + wr], m);
+        n3 = i3;
+        n1 = i1;
+    }
+    finish_quad<SOLID, FORCE, RAGGED>(a, q, y, m, n0, n1, n2, n3, n4, n5, i6, sd, true);
+}
+
+template <bool SOLID, bool FORCE, bool RAGGED>
+__device__ __forceinline__ void compute_tile(const StepArgs& a, const TileArgs& ta, int tile,
+                                             const uint32_t* stage) {
+    const int y0 = tile * ta.R;
+    const int rows = min(ta.R, a.H - y0);
+    // Items ordered even local rows first, then odd ones, so that the row
+    // parity (which selects the shift pattern) is uniform within a warp.
+    const int even_rows = (rows + 1) >> 1;
+    const int even_items = even_rows * a.nq;
+    const int items = rows * a.nq;
+    for (int it = threadIdx.x; it < items; it += blockDim.x) {
+        const int h = it >= even_items;
+        const uint32_t j = (uint32_t)(h ? it - even_items : it);
+        const int k = (int)(((unsigned long long)j * ta.nq_magic) >> 32);  // j / nq
+        const int q = (int)j - k * a.nq;
+        const int r = 2 * k + h;
+        quad_from_stage<SOLID, FORCE, RAGGED>(a, ta, stage, r, y0 + r, q);
+    }
+}
+
+template <bool SOLID, bool FORCE, bool RAGGED>
+__global__ void __launch_bounds__(kTmaThreads, 2) fhp_step_tma_kernel(const StepArgs a, const TileArgs ta) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw);
+    uint32_t* stages = reinterpret_cast<uint32_t*>(smem_raw + kBarrierBytes);
+    constexpr int NP = SOLID ? 8 : 7;
+    const size_t stage_words = (size_t)NP * ta.R * a.Pq;
+    // Tiles of this CTA: blockIdx.x, blockIdx.x + gridDim.x, ...
+    const int count = (ta.ntiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
+    auto tile_of = [&](int i) { return (int)blockIdx.x + i * (int)gridDim.x; };
+    auto stage_of = [&](int i) { return stages + (size_t)(i % kStages) * stage_words; };
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStages; ++s) mbar_init(&bars[s], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    int issued = 0;
+    if (threadIdx.x == 0) {
+        for (; issued < kStages && issued < count; ++issued)
+            issue_tile<SOLID>(a, ta, tile_of(issued), stage_of(issued), &bars[issued % kStages]);
+    }
+    int abort_from = -1;
+    if (count > 0) {
+        const bool ok = mbar_wait_bounded(&bars[0], 0u);
+        if (__syncthreads_or(!ok)) abort_from = 0;
+    }
+    for (int i = 0; abort_from < 0 && i < count; ++i) {
+        compute_tile<SOLID, FORCE, RAGGED>(a, ta, tile_of(i), stage_of(i));
+        bool ok = true;
+        if (i + 1 < count) ok = mbar_wait_bounded(&bars[(i + 1) % kStages], (uint32_t)(((i + 1) / kStages) & 1));
+        // Everyone is done with stage i % kStages (and has seen tile i+1 land).
+        if (__syncthreads_or(!ok)) {
+            abort_from = i + 1;
+            break;
+        }
+        if (threadIdx.x == 0 && issued < count) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            issue_tile<SOLID>(a, ta, tile_of(issued), stage_of(issued), &bars[issued % kStages]);
+            ++issued;
+        }
+    }
+    if (abort_from >= 0 && threadIdx.x == 0) {
+        // A copy never completed: report it, and do not leave the CTA while
+        // copies into its shared memory may still be in flight.
+        if (a.err) atomicOr(a.err, 1u);
+        for (int k = abort_from; k < issued; ++k)
+            (void)mbar_wait_bounded(&bars[k % kStages], (uint32_t)((k / kStages) & 1));
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Direct kernel: one quad per thread, neighbour words by warp shuffles.
+// ---------------------------------------------------------------------------
 struct Lane {
     int y, q;
     bool active;
-    int src_left, src_right;   // lanes holding the quads to the left / right
+    int src_left, src_right;     // lanes holding the quads to the left / right
     bool glob_left, glob_right;  // neighbour quad outside the warp: load it
 };
 
@@ -65,42 +348,21 @@ __device__ __forceinline__ Lane map_lane(const StepArgs& a) {
     return L;
 }
 
-__device__ __forceinline__ uint4 ld4(const uint32_t* p) {
-    return *reinterpret_cast<const uint4*>(p);
-}
-
-__device__ __forceinline__ void st4(uint32_t* p, uint4 v) {
-    *reinterpret_cast<uint4*>(p) = v;
-}
-
-// New bit x takes old bit x-1.  `m` = number of valid words in this quad.
 template <bool RAGGED>
-__device__ __forceinline__ uint4 from_left(uint4 v, uint32_t fallback, const Lane& L, int m) {
-    uint32_t offer = v.w;
+__device__ __forceinline__ uint32_t left_word(uint4 v, uint32_t fallback, const Lane& L, int m) {
+    uint32_t offer = v.w;  // the quad's last valid word, for the lane to the right
     if (RAGGED) offer = m == 4 ? v.w : m == 3 ? v.z : m == 2 ? v.y : v.x;
-    uint32_t left = __shfl_sync(kFull, offer, L.src_left);
-    if (L.glob_left) left = fallback;
-    return make_uint4(__funnelshift_l(left, v.x, 1), __funnelshift_l(v.x, v.y, 1),
-                      __funnelshift_l(v.y, v.z, 1), __funnelshift_l(v.z, v.w, 1));
+    const uint32_t left = __shfl_sync(kFull, offer, L.src_left);
+    return L.glob_left ? fallback : left;
 }
 
-// New bit x takes old bit x+1.
-template <bool RAGGED>
-__device__ __forceinline__ uint4 from_right(uint4 v, uint32_t fallback, const Lane& L, int m) {
-    uint32_t right = __shfl_sync(kFull, v.x, L.src_right);
-    if (L.glob_right) right = fallback;
-    uint32_t n0 = v.y, n1 = v.z, n2 = v.w;
-    if (RAGGED) {
-        if (m == 1) n0 = right;
-        if (m == 2) n1 = right;
-        if (m == 3) n2 = right;
-    }
-    return make_uint4(__funnelshift_r(v.x, n0, 1), __funnelshift_r(v.y, n1, 1),
-                      __funnelshift_r(v.z, n2, 1), __funnelshift_r(v.w, right, 1));
+__device__ __forceinline__ uint32_t right_word(uint4 v, uint32_t fallback, const Lane& L) {
+    const uint32_t right = __shfl_sync(kFull, v.x, L.src_right);
+    return L.glob_right ? fallback : right;
 }
 
 template <bool SOLID, bool FORCE, bool RAGGED, bool ODD>
-__device__ __forceinline__ void step_quad(const StepArgs& a, const Lane& L) {
+__device__ __forceinline__ void direct_quad(const StepArgs& a, const Lane& L) {
     const size_t pw = a.plane_words;
     const int y = L.y;
     const int ym = y == 0 ? a.H - 1 : y - 1;
@@ -110,11 +372,9 @@ __device__ __forceinline__ void step_quad(const StepArgs& a, const Lane& L) {
     const uint32_t* r0 = a.src + (size_t)y * a.Pq;   // row y
     const uint32_t* rp = a.src + (size_t)yp * a.Pq;  // row y+1
     const int m = RAGGED ? (L.q == a.nq - 1 ? a.Wq - w : 4) : 4;
-    const int wl = L.q == 0 ? a.Wq - 1 : w - 1;      // word left of the quad (periodic)
-    const int wr = L.q == a.nq - 1 ? 0 : w + 4;      // word right of the quad (periodic)
+    const int wl = L.q == 0 ? a.Wq - 1 : w - 1;
+    const int wr = L.q == a.nq - 1 ? 0 : w + 4;
 
-    // Rows y-1 feed the upward movers (NE 3, NW 4), row y the horizontal movers
-    // (E 2, W 5) and the rest particle, row y+1 the downward movers (SW 0, SE 1).
     const uint4 i3 = ld4(rm + 3 * pw + w), i4 = ld4(rm + 4 * pw + w);
     const uint4 i2 = ld4(r0 + 2 * pw + w), i5 = ld4(r0 + 5 * pw + w);
     const uint4 i6 = ld4(r0 + 6 * pw + w);
@@ -124,81 +384,34 @@ __device__ __forceinline__ void step_quad(const StepArgs& a, const Lane& L) {
 
     uint4 n0, n1, n2, n3, n4, n5;
     if (!ODD) {
-        // Even row: E, NE, SE come from x-1; W from x+1; NW, SW from x.
         uint32_t f2 = 0, f3 = 0, f1 = 0, f5 = 0;
         if (L.glob_left) { f2 = r0[2 * pw + wl]; f3 = rm[3 * pw + wl]; f1 = rp[1 * pw + wl]; }
         if (L.glob_right) f5 = r0[5 * pw + wr];
-        n2 = from_left<RAGGED>(i2, f2, L, m);
-        n3 = from_left<RAGGED>(i3, f3, L, m);
-        n1 = from_left<RAGGED>(i1, f1, L, m);
-        n5 = from_right<RAGGED>(i5, f5, L, m);
+        n2 = pull_left(i2, left_word<RAGGED>(i2, f2, L, m));
+        n3 = pull_left(i3, left_word<RAGGED>(i3, f3, L, m));
+        n1 = pull_left(i1, left_word<RAGGED>(i1, f1, L, m));
+        n5 = pull_right<RAGGED>(i5, right_word(i5, f5, L), m);
         n4 = i4;
         n0 = i0;
     } else {
-        // Odd row: E from x-1; W, NW, SW from x+1; NE, SE from x.
         uint32_t f2 = 0, f5 = 0, f4 = 0, f0 = 0;
         if (L.glob_left) f2 = r0[2 * pw + wl];
         if (L.glob_right) { f5 = r0[5 * pw + wr]; f4 = rm[4 * pw + wr]; f0 = rp[0 * pw + wr]; }
-        n2 = from_left<RAGGED>(i2, f2, L, m);
-        n5 = from_right<RAGGED>(i5, f5, L, m);
-        n4 = from_right<RAGGED>(i4, f4, L, m);
-        n0 = from_right<RAGGED>(i0, f0, L, m);
+        n2 = pull_left(i2, left_word<RAGGED>(i2, f2, L, m));
+        n5 = pull_right<RAGGED>(i5, right_word(i5, f5, L), m);
+        n4 = pull_right<RAGGED>(i4, right_word(i4, f4, L), m);
+        n0 = pull_right<RAGGED>(i0, right_word(i0, f0, L), m);
         n3 = i3;
         n1 = i1;
     }
-
-    const uint4 chi = rng_block((uint32_t)L.q, (uint32_t)y, a.t_lo, a.t_hi, 0u, a.key);
-    uint4 gate = make_uint4(0u, 0u, 0u, 0u);
-    if (FORCE) gate = rng_block((uint32_t)L.q, (uint32_t)y, a.t_lo, a.t_hi, 1u, a.key);
-
-    uint4 o0, o1, o2, o3, o4, o5, o6;
-#define FHP_WORD(J, C)                                                                          \
-    {                                                                                           \
-        Planes7 in{n0.C, n1.C, n2.C, n3.C, n4.C, n5.C, i6.C};                                   \
-        Planes7 out = scatter(in, sd.C, chi.C);                                                 \
-        if (FORCE) {                                                                            \
-            const uint32_t cand = ~sd.C & out.m5 & ~out.m2;                                     \
-            const uint32_t u = gate.C;                                                          \
-            if (cand != 0u && (unsigned long long)u < a.ft.q[32]) {                             \
-                const uint32_t f = forced_mask(cand, u, a.ft, [&](uint32_t d) {                 \
-                    return word_of(rng_block((uint32_t)L.q, (uint32_t)y, a.t_lo, a.t_hi, 1u + d, \
-                                             a.key), J);                                        \
-                });                                                                             \
-                out.m5 ^= f;                                                                    \
-                out.m2 ^= f;                                                                    \
-            }                                                                                   \
-        }                                                                                       \
-        o0.C = out.m0; o1.C = out.m1; o2.C = out.m2; o3.C = out.m3;                             \
-        o4.C = out.m4; o5.C = out.m5; o6.C = out.rest;                                          \
-    }
-    FHP_WORD(0, x)
-    FHP_WORD(1, y)
-    FHP_WORD(2, z)
-    FHP_WORD(3, w)
-#undef FHP_WORD
-
-    if (!L.active) return;
-    if (RAGGED && m < 4) {
-        // Keep the padding words of the last quad zero.
-        if (m < 2) { o0.y = o1.y = o2.y = o3.y = o4.y = o5.y = o6.y = 0u; }
-        if (m < 3) { o0.z = o1.z = o2.z = o3.z = o4.z = o5.z = o6.z = 0u; }
-        o0.w = o1.w = o2.w = o3.w = o4.w = o5.w = o6.w = 0u;
-    }
-    uint32_t* d = a.dst + (size_t)y * a.Pq + w;
-    st4(d + 0 * pw, o0);
-    st4(d + 1 * pw, o1);
-    st4(d + 2 * pw, o2);
-    st4(d + 3 * pw, o3);
-    st4(d + 4 * pw, o4);
-    st4(d + 5 * pw, o5);
-    st4(d + 6 * pw, o6);
+    finish_quad<SOLID, FORCE, RAGGED>(a, L.q, y, m, n0, n1, n2, n3, n4, n5, i6, sd, L.active);
 }
 
 template <bool SOLID, bool FORCE, bool RAGGED>
-__global__ void __launch_bounds__(kBlock) fhp_step_kernel(const StepArgs a) {
+__global__ void __launch_bounds__(kBlock) fhp_step_direct_kernel(const StepArgs a) {
     const Lane L = map_lane(a);
-    if (L.y & 1) step_quad<SOLID, FORCE, RAGGED, true>(a, L);
-    else step_quad<SOLID, FORCE, RAGGED, false>(a, L);
+    if (L.y & 1) direct_quad<SOLID, FORCE, RAGGED, true>(a, L);
+    else direct_quad<SOLID, FORCE, RAGGED, false>(a, L);
 }
 
 __global__ void philox_kernel(const uint32_t* __restrict__ ctr, const uint32_t* __restrict__ key,
@@ -214,13 +427,73 @@ __global__ void philox_kernel(const uint32_t* __restrict__ ctr, const uint32_t* 
     }
 }
 
+// ---------------------------------------------------------------------------
+// Host side.
+// ---------------------------------------------------------------------------
+struct DeviceInfo {
+    int sms = 0;
+    int tma_blocks_per_sm[8] = {};  // per kernel variant (solid, force, ragged)
+    bool configured[8] = {};
+};
+std::mutex g_dev_mutex;
+DeviceInfo g_dev[64];
+
+template <bool SOLID, bool FORCE, bool RAGGED>
+cudaError_t launch_tma_variant(const StepArgs& a, const TileArgs& ta, size_t smem, cudaStream_t s) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    const int variant = (SOLID ? 4 : 0) | (FORCE ? 2 : 0) | (RAGGED ? 1 : 0);
+    auto kernel = fhp_step_tma_kernel<SOLID, FORCE, RAGGED>;
+    int blocks_per_sm, sms;
+    {
+        std::lock_guard<std::mutex> lock(g_dev_mutex);
+        DeviceInfo& d = g_dev[dev];
+        if (!d.sms) {
+            e = cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev);
+            if (e != cudaSuccess) return e;
+        }
+        if (!d.configured[variant]) {
+            const int max_smem = kBarrierBytes + kStages * kStageBudget;
+            e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+            if (e != cudaSuccess) return e;
+            int n = 0;
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, kTmaThreads, max_smem);
+            if (e != cudaSuccess) return e;
+            d.tma_blocks_per_sm[variant] = n > 0 ? n : 1;
+            d.configured[variant] = true;
+        }
+        blocks_per_sm = d.tma_blocks_per_sm[variant];
+        sms = d.sms;
+    }
+    const int grid = min(ta.ntiles, blocks_per_sm * sms);
+    kernel<<<grid, kTmaThreads, smem, s>>>(a, ta);
+    return cudaGetLastError();
+}
+
 template <bool SOLID, bool FORCE>
-cudaError_t launch_variant(const StepArgs& a, bool ragged, long long warps, cudaStream_t s) {
+cudaError_t launch_tma(const StepArgs& a, const TileArgs& ta, size_t smem, bool ragged, cudaStream_t s) {
+    return ragged ? launch_tma_variant<SOLID, FORCE, true>(a, ta, smem, s)
+                  : launch_tma_variant<SOLID, FORCE, false>(a, ta, smem, s);
+}
+
+template <bool SOLID, bool FORCE>
+cudaError_t launch_direct(const StepArgs& a, bool ragged, long long warps, cudaStream_t s) {
     const long long threads = warps * 32;
     const unsigned grid = (unsigned)((threads + kBlock - 1) / kBlock);
-    if (ragged) fhp_step_kernel<SOLID, FORCE, true><<<grid, kBlock, 0, s>>>(a);
-    else fhp_step_kernel<SOLID, FORCE, false><<<grid, kBlock, 0, s>>>(a);
+    if (ragged) fhp_step_direct_kernel<SOLID, FORCE, true><<<grid, kBlock, 0, s>>>(a);
+    else fhp_step_direct_kernel<SOLID, FORCE, false><<<grid, kBlock, 0, s>>>(a);
     return cudaGetLastError();
+}
+
+// Rows per tile of the bulk-copy kernel, or 0 if one row does not fit a stage.
+int tile_rows(const Geometry& g, bool has_solid) {
+    const int np = has_solid ? 8 : 7;
+    const long long row_bytes = (long long)np * g.Pq * 4;
+    if (row_bytes > kStageBudget) return 0;
+    int R = (int)(kStageBudget / row_bytes);
+    return R < g.H ? R : g.H;
 }
 
 }  // namespace
@@ -244,9 +517,27 @@ Geometry make_geometry(int W, int H) {
     return g;
 }
 
+int resolved_step_kernel(const Geometry& g, bool has_solid, int requested) {
+    const int R = tile_rows(g, has_solid);
+    if (R == 0 || requested == kStepDirect) return kStepDirect;
+    if (requested == kStepRing) return kStepRing;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return kStepDirect;
+    {
+        std::lock_guard<std::mutex> lock(g_dev_mutex);
+        if (!g_dev[dev].sms && cudaDeviceGetAttribute(&g_dev[dev].sms, cudaDevAttrMultiProcessorCount, dev) !=
+                                   cudaSuccess)
+            return kStepDirect;
+        sms = g_dev[dev].sms;
+    }
+    const int ntiles = (g.H + R - 1) / R;
+    return ntiles >= 2 * sms ? kStepRing : kStepDirect;
+}
+
 cudaError_t launch_step(const Geometry& g, const uint32_t* src, uint32_t* dst,
                         const uint32_t* solid, bool has_solid, bool force,
-                        const ForcingTable& ft, Key2 key, uint64_t t, cudaStream_t stream) {
+                        const ForcingTable& ft, Key2 key, uint64_t t, cudaStream_t stream,
+                        unsigned int* err, int kernel) {
     StepArgs a;
     a.src = src;
     a.dst = dst;
@@ -256,6 +547,26 @@ cudaError_t launch_step(const Geometry& g, const uint32_t* src, uint32_t* dst,
     a.Wq = g.Wq;
     a.nq = g.nq;
     a.Pq = g.Pq;
+    a.key = key;
+    a.t_lo = (uint32_t)t;
+    a.t_hi = (uint32_t)(t >> 32);
+    a.err = err;
+    a.ft = ft;
+    const bool ragged = (g.Wq % 4) != 0;
+    const int R = tile_rows(g, has_solid);
+    if (resolved_step_kernel(g, has_solid, kernel) == kStepRing) {
+        TileArgs ta;
+        ta.R = R;
+        ta.ntiles = (g.H + R - 1) / R;
+        ta.nq_magic = ((1ull << 32) + g.nq - 1) / g.nq;
+        a.rows_per_warp = a.groups_per_parity = a.warps_per_row = 1;
+        const size_t smem = kBarrierBytes + (size_t)kStages * (has_solid ? 8 : 7) * R * g.Pq * 4;
+        if (has_solid)
+            return force ? launch_tma<true, true>(a, ta, smem, ragged, stream)
+                         : launch_tma<true, false>(a, ta, smem, ragged, stream);
+        return force ? launch_tma<false, true>(a, ta, smem, ragged, stream)
+                     : launch_tma<false, false>(a, ta, smem, ragged, stream);
+    }
     long long warps;
     if (g.nq >= 32) {
         a.warps_per_row = (g.nq + 31) / 32;
@@ -268,17 +579,11 @@ cudaError_t launch_step(const Geometry& g, const uint32_t* src, uint32_t* dst,
         a.groups_per_parity = ((g.H / 2) + a.rows_per_warp - 1) / a.rows_per_warp;
         warps = 2LL * a.groups_per_parity;
     }
-    a.key = key;
-    a.t_lo = (uint32_t)t;
-    a.t_hi = (uint32_t)(t >> 32);
-    a.ft = ft;
-    const bool ragged = (g.Wq % 4) != 0;
-    if (has_solid) {
-        return force ? launch_variant<true, true>(a, ragged, warps, stream)
-                     : launch_variant<true, false>(a, ragged, warps, stream);
-    }
-    return force ? launch_variant<false, true>(a, ragged, warps, stream)
-                 : launch_variant<false, false>(a, ragged, warps, stream);
+    if (has_solid)
+        return force ? launch_direct<true, true>(a, ragged, warps, stream)
+                     : launch_direct<true, false>(a, ragged, warps, stream);
+    return force ? launch_direct<false, true>(a, ragged, warps, stream)
+                 : launch_direct<false, false>(a, ragged, warps, stream);
 }
 
 }  // namespace fhp

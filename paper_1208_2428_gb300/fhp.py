@@ -73,6 +73,8 @@ def load(path: str | None = None):
         "fhp_set_forcing": (ctypes.c_int, [vp, ctypes.c_double]),
         "fhp_set_temporal_block": (ctypes.c_int, [vp, i32]),
         "fhp_synchronize": (ctypes.c_int, [vp]),
+        "fhp_set_step_kernel": (ctypes.c_int, [vp, i32]),
+        "fhp_get_step_kernel": (ctypes.c_int, [vp]),
         "fhp_kernel_launches": (i64, [vp]),
         "fhp_philox4x32_10_device": (ctypes.c_int, [vp, vp, vp, i64, vp]),
     }
@@ -107,7 +109,7 @@ class Lattice:
     """
 
     def __init__(self, width: int, height: int, seed: int = 0, forcing_p: float = 0.0,
-                 device=None, stream=None):
+                 device=None, stream=None, step_kernel: int = 0):
         torch = _torch()
         self._lib = load()
         self.width, self.height = int(width), int(height)
@@ -130,6 +132,8 @@ class Lattice:
         self._h = h
         self.seed = int(seed)
         self.forcing_p = float(forcing_p)
+        if step_kernel:
+            self.set_step_kernel(step_kernel)
 
     # -- plumbing -------------------------------------------------------------
     def _check(self, rc: int):
@@ -207,6 +211,14 @@ class Lattice:
 
     def set_temporal_block(self, k: int):
         self._check(self._lib.fhp_set_temporal_block(self._h, int(k)))
+
+    def set_step_kernel(self, kind: int):
+        """0 automatic, 1 direct register loads, 2 bulk-copy shared-memory ring."""
+        self._check(self._lib.fhp_set_step_kernel(self._h, int(kind)))
+
+    @property
+    def step_kernel(self) -> int:
+        return int(self._lib.fhp_get_step_kernel(self._h))
 
     def synchronize(self):
         self._check(self._lib.fhp_synchronize(self._h))

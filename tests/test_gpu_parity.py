@@ -27,9 +27,9 @@ def fhp_mod():
     return pkg
 
 
-def gpu_run(pkg, s0, seed, t0, n, p, chunks=None):
+def gpu_run(pkg, s0, seed, t0, n, p, chunks=None, kernel=0):
     H, W = s0.shape
-    with pkg.Lattice(W, H, seed=seed, forcing_p=p) as lat:
+    with pkg.Lattice(W, H, seed=seed, forcing_p=p, step_kernel=kernel) as lat:
         lat.set_state(s0)
         lat.set_time(t0)
         for c in (chunks or [n]):
@@ -64,9 +64,13 @@ SHAPES = [
 ]
 
 
+KERNELS = [1, 2]   # direct register loads; bulk-copy shared-memory ring
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
 @pytest.mark.parametrize("W,H", SHAPES)
 @pytest.mark.parametrize("variant", ["periodic", "walls_forcing", "points_forcing"])
-def test_parity_shapes(fhp_mod, oracle_mod, W, H, variant):
+def test_parity_shapes(fhp_mod, oracle_mod, W, H, variant, kernel):
     seed = 1000 + W + 7 * H
     rng = np.random.Generator(np.random.PCG64(seed))
     if variant == "periodic":
@@ -78,20 +82,31 @@ def test_parity_shapes(fhp_mod, oracle_mod, W, H, variant):
     s0 = workloads.bernoulli_lattice(W, H, 0.35, seed, solid)
     steps = 9
     want, _ = oracle_mod.run(s0, seed, 3, steps, p)
-    got = gpu_run(fhp_mod, s0, seed, 3, steps, p)
-    assert_same(got, want, f"{W}x{H} {variant}")
+    got = gpu_run(fhp_mod, s0, seed, 3, steps, p, kernel=kernel)
+    assert_same(got, want, f"{W}x{H} {variant} kernel {kernel}")
 
 
-def test_parity_empty_and_full(fhp_mod, oracle_mod):
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_parity_empty_and_full(fhp_mod, oracle_mod, kernel):
     for W, H in [(64, 4), (4160, 2)]:
         for fill in (0x00, 0x7F, 0x3F, 0x40):
             s0 = np.full((H, W), fill, dtype=np.uint8)
             want, _ = oracle_mod.run(s0, 3, 0, 5, 0.5)
-            got = gpu_run(fhp_mod, s0, 3, 0, 5, 0.5)
+            got = gpu_run(fhp_mod, s0, 3, 0, 5, 0.5, kernel=kernel)
             assert_same(got, want, f"fill {fill:#x}")
         s0 = np.full((H, W), 0xFF, dtype=np.uint8)   # all solid, full of particles
         want, _ = oracle_mod.run(s0, 3, 0, 4, 0.5)
-        assert_same(gpu_run(fhp_mod, s0, 3, 0, 4, 0.5), want, "all solid")
+        assert_same(gpu_run(fhp_mod, s0, 3, 0, 4, 0.5, kernel=kernel), want, "all solid")
+
+
+@pytest.mark.parametrize("W,H", [(256, 2048), (4096, 1024), (2048, 512), (96, 4096)])
+def test_parity_ring_many_tiles(fhp_mod, oracle_mod, W, H):
+    """Shapes where the ring kernel walks many tiles per CTA (pipeline wrap-around)."""
+    seed = W + H
+    s0 = workloads.bernoulli_lattice(W, H, 0.3, seed, workloads.cylinder_mask(W, H))
+    want, _ = oracle_mod.run(s0, seed, 0, 6, 0.01)
+    got = gpu_run(fhp_mod, s0, seed, 0, 6, 0.01, kernel=2)
+    assert_same(got, want, f"ring {W}x{H}")
 
 
 def test_parity_large_step_counter(fhp_mod, oracle_mod):
@@ -143,13 +158,28 @@ def test_channel_coarse_grain(fhp_mod, oracle_mod):
 
 def test_cylinder_full_size(fhp_mod, oracle_mod):
     """16384 x 4096 cylinder workload at full size in the benchmark's launch
-    configuration: whole state bit-exact after 12 steps."""
+    configuration (automatic kernel choice, as bench.py runs it): whole state
+    bit-exact after 12 steps; the direct kernel agrees too."""
     job = workloads.cylinder_16384x4096()
     s0 = job.initial_state()
     n = 12
     want, ev = oracle_mod.run(s0, job.seed, 0, n, job.p)
-    got = gpu_run(fhp_mod, s0, job.seed, 0, n, job.p)
-    assert_same(got, want, "cylinder 16384x4096")
+    with fhp_mod.Lattice(job.W, job.H, seed=job.seed, forcing_p=job.p) as lat:
+        lat.set_state(s0)
+        assert lat.step_kernel == 2      # the ring kernel is what the benchmark times
+        lat.step(n)
+        assert_same(lat.get_state(), want, "cylinder 16384x4096")
+    assert_same(gpu_run(fhp_mod, s0, job.seed, 0, n, job.p, kernel=1), want, "cylinder, direct kernel")
+
+
+def test_paper_size_lattice(fhp_mod, oracle_mod):
+    """The paper's GPU lattice size (29,970 x 27,990; W rounded up to 29,984,
+    a ragged row of 937 words): 2 steps bit-exact."""
+    job = workloads.cylinder_paper_size()
+    s0 = job.initial_state()
+    want, _ = oracle_mod.run(s0, job.seed, 0, 2, job.p)
+    got = gpu_run(fhp_mod, s0, job.seed, 0, 2, job.p)
+    assert_same(got, want, "29984 x 27990")
 
 
 def test_resume_from_checkpoint(fhp_mod):
