@@ -49,7 +49,8 @@ def parse_args():
     ap.add_argument("--lattice-steps", type=int, default=None,
                     help="time steps per benchmark step (default: the workload's run length)")
     ap.add_argument("--temporal-block", type=int, default=1)
-    ap.add_argument("--step-kernel", type=int, default=0, help="0 auto, 1 direct, 2 bulk-copy ring")
+    ap.add_argument("--step-kernel", type=int, default=0,
+                    help="0 auto, 1 direct, 2 bulk-copy ring, 3 multi-step ring")
     ap.add_argument("--cg-block", type=int, default=32)
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="target CPU time of the oracle baseline sample")
@@ -82,9 +83,10 @@ def source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(workload_name: str):
-    """DRAM bytes per launch of the step kernel from the committed ncu summary,
-    if it was taken on the current kernel source."""
+def recorded_traffic(workload_name: str, steps_per_launch: float):
+    """DRAM bytes per launch of the step kernel from the committed ncu summary
+    (recorded per lattice step of the workload), if it was taken on the
+    current kernel source."""
     path = os.path.join(ROOT, "profiles", f"fhp_step_{workload_name}.txt")
     try:
         fields = {}
@@ -95,7 +97,7 @@ def recorded_traffic(workload_name: str):
                     fields[k.strip()] = v.strip()
         if fields.get("source_hash") != source_hash():
             return None
-        return float(fields["dram_bytes_per_launch_full_size"])
+        return float(fields["dram_bytes_per_lattice_step_full_size"]) * steps_per_launch
     except Exception:
         return None
 
@@ -299,7 +301,8 @@ def run_gpu(args):
         dist.barrier()
     launches = lat.kernel_launches - launches0
     clocks = sampler.stop()
-    kernel_name = {1: "fhp_step_direct_kernel", 2: "fhp_step_tma_kernel"}.get(lat.step_kernel, "?")
+    kernel_name = {1: "fhp_step_direct_kernel", 2: "fhp_step_tma_kernel", 3: "fhp_run_kernel"}.get(
+        lat.step_kernel, "?")
     total_ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
     step_kernel_ms = sum(s.elapsed_time(m) for s, m in zip(starts, mids))
     if dist:
@@ -310,10 +313,17 @@ def run_gpu(args):
     nodes = job.W * job.H
     value = world * nodes * nsteps * args.steps / (total_ms / 1e3) / 1e9
     bytes_per_node = (14 + (1 if has_solid else 0)) / 8.0
-    launch_s = step_kernel_ms / 1e3 / (args.steps * nsteps)
-    achieved = bytes_per_node * nodes / launch_s / 1e9
+    # Step-kernel launches in the timed region: one per lattice step for the
+    # single-step kernels, one per fhp_step call (chunks of 2^24 steps) for
+    # the multi-step kernel.
+    cg_launches = args.steps if B else 0
+    step_launches = max(1, launches - cg_launches)
+    steps_per_launch = nsteps * args.steps / step_launches
+    launch_s = step_kernel_ms / 1e3 / step_launches
+    bytes_per_launch = bytes_per_node * nodes * steps_per_launch
+    achieved = bytes_per_launch / launch_s / 1e9
     peak, peak_src = measured_hbm_peak()
-    traffic = recorded_traffic(job.name)
+    traffic = recorded_traffic(job.name, steps_per_launch)
 
     # End to end through the C ABI with host buffers: pinned initial state in,
     # coarse-grained fields out, host<->device copies inside the timed region.
@@ -369,9 +379,11 @@ def run_gpu(args):
                              "set is below the 126 MB L2 within a step"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
-                         "kernel": kernel_name, "algorithmic_bytes_per_node": bytes_per_node,
-                         "peak_source": peak_src,
-                         "launch_us": launch_s * 1e6},
+                         "kernel": kernel_name, "algorithmic_bytes_per_node_step": bytes_per_node,
+                         "lattice_steps_per_launch": steps_per_launch,
+                         "algorithmic_bytes_per_launch": bytes_per_launch,
+                         "launch_duration_us": launch_s * 1e6,
+                         "peak_source": peak_src},
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": launches,

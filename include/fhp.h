@@ -65,9 +65,9 @@ typedef struct fhp_params {
 } fhp_params;
 
 /* Bytes of device memory one lattice of W x H nodes uses: two bit-plane
- * state buffers (7 planes each), one solid plane, and a W*H-byte staging
- * area for transfers and coarse-grained results.  Returns 0 for invalid
- * sizes. */
+ * state buffers (7 planes each), one solid plane, H counter words for the
+ * multi-step kernel, and a W*H-byte staging area for transfers and
+ * coarse-grained results.  Returns 0 for invalid sizes. */
 FHP_API size_t fhp_required_bytes(int32_t width, int32_t height);
 
 /* Create a lattice on the current CUDA device with all nodes empty and
@@ -148,12 +148,16 @@ FHP_API int fhp_set_temporal_block(fhp_lattice* lattice, int32_t k);
 /* Step kernel used by fhp_step: 0 = automatic (default), 1 = direct (one
  * 128-node quad per thread, operands loaded into registers), 2 = bulk-copy
  * ring (persistent CTAs stage tiles of full rows in shared memory with
- * cp.async.bulk; falls back to 1 when a row does not fit a stage).  Results
- * are identical for every choice. */
+ * cp.async.bulk, one launch per step), 3 = multi-step ring (the ring kernel
+ * running all steps of an fhp_step call in one cooperative launch, each tile
+ * waiting only for the three tiles of the previous step it reads).  2 and 3
+ * fall back to 1 when a row does not fit a stage; automatic picks 3 when the
+ * lattice has at least two tiles per SM, else 1.  Results are identical for
+ * every choice. */
 FHP_API int fhp_set_step_kernel(fhp_lattice* lattice, int32_t kind);
 
 /* The step kernel fhp_step will run for the lattice's current settings
- * (1 or 2), or -1 for a NULL lattice. */
+ * (1, 2 or 3), or -1 for a NULL lattice. */
 FHP_API int fhp_get_step_kernel(const fhp_lattice* lattice);
 
 /* Block the calling thread until all work queued on the lattice's stream

@@ -31,6 +31,7 @@ struct fhp_lattice {
     unsigned int* flags = nullptr;  // device words: [0] any solid node, [1] kernel wait gave up
     uint8_t* staging = nullptr;
     size_t staging_bytes = 0;
+    unsigned int* tile_done = nullptr;  // multi-step kernel: per-tile counters (H words)
     int cur = 0;
     int64_t t = 0;
     bool has_solid = false;
@@ -66,7 +67,7 @@ bool valid_size(int32_t W, int32_t H) {
 }
 
 struct Layout {
-    size_t plane_bytes, state_bytes, solid_off, flags_off, staging_off, staging_bytes, total;
+    size_t plane_bytes, state_bytes, solid_off, flags_off, counters_off, staging_off, staging_bytes, total;
 };
 
 Layout layout(int32_t W, int32_t H) {
@@ -76,7 +77,8 @@ Layout layout(int32_t W, int32_t H) {
     L.state_bytes = 7 * L.plane_bytes;
     L.solid_off = 2 * L.state_bytes;
     L.flags_off = L.solid_off + L.plane_bytes;
-    L.staging_off = L.flags_off + 256;
+    L.counters_off = L.flags_off + 256;  // one word per row covers any tiling
+    L.staging_off = L.counters_off + round_up((size_t)H * sizeof(unsigned int), 256);
     L.staging_bytes = round_up((size_t)W * H, 256);
     L.total = L.staging_off + L.staging_bytes;
     return L;
@@ -93,6 +95,7 @@ fhp::ForcingTable forcing_table(double p) {
     else P = (unsigned long long)std::nearbyint(scaled);  // default mode: nearest, ties to even
     fhp::ForcingTable ft;
     unsigned long long S = one;
+    ft.p_plus_1 = P + 1;
     ft.q[0] = 0;
     for (int g = 1; g <= 32; ++g) {
         S = (unsigned long long)(((unsigned __int128)S * (one - P)) >> 32);
@@ -201,6 +204,7 @@ int fhp_create(fhp_lattice** out, const fhp_params* params) {
     h->buf[1] = (uint32_t*)(h->base + L.state_bytes);
     h->solid = (uint32_t*)(h->base + L.solid_off);
     h->flags = (unsigned int*)(h->base + L.flags_off);
+    h->tile_done = (unsigned int*)(h->base + L.counters_off);
     h->staging = h->base + L.staging_off;
     h->staging_bytes = L.staging_bytes;
     // Empty fluid lattice: zero both buffers and the solid plane.
@@ -291,6 +295,22 @@ int fhp_step(fhp_lattice* h, int64_t n) {
     if (n > kMaxTime - h->t) return fail(h, FHP_EINVAL, "step counter would pass 2^48");
     DeviceGuard dg(h->device);
     const fhp::Key2 key{(uint32_t)h->seed, (uint32_t)(h->seed >> 32)};
+    if (n >= 2 && fhp::resolved_step_kernel(h->g, h->has_solid, h->step_kernel) == fhp::kStepRun) {
+        // All n steps in cooperative launches of up to 2^24 steps each.
+        int64_t left = n;
+        while (left > 0) {
+            const int chunk = (int)(left < (1 << 24) ? left : (1 << 24));
+            cudaError_t e = fhp::launch_run(h->g, h->buf[h->cur], h->buf[h->cur ^ 1], h->solid, h->has_solid,
+                                            h->force, h->ft, key, (uint64_t)h->t, chunk, h->tile_done,
+                                            h->stream, h->flags + 1);
+            if (e != cudaSuccess) return cuda_fail(h, e, "launching the multi-step kernel");
+            ++h->launches;
+            h->cur ^= (chunk & 1);
+            h->t += chunk;
+            left -= chunk;
+        }
+        return FHP_OK;
+    }
     for (int64_t i = 0; i < n; ++i) {
         cudaError_t e = fhp::launch_step(h->g, h->buf[h->cur], h->buf[h->cur ^ 1], h->solid, h->has_solid,
                                          h->force, h->ft, key, (uint64_t)h->t, h->stream, h->flags + 1,
@@ -369,7 +389,7 @@ int fhp_set_temporal_block(fhp_lattice* h, int32_t k) {
 
 int fhp_set_step_kernel(fhp_lattice* h, int32_t kind) {
     if (!h) return fail(nullptr, FHP_EINVAL, "lattice is NULL");
-    if (kind < 0 || kind > 2) return fail(h, FHP_EINVAL, "step kernel %d not in {0, 1, 2}", kind);
+    if (kind < 0 || kind > 3) return fail(h, FHP_EINVAL, "step kernel %d not in {0, 1, 2, 3}", kind);
     h->step_kernel = kind;
     return FHP_OK;
 }

@@ -22,6 +22,9 @@ struct Key2 {
 
 struct ForcingTable {
     unsigned long long q[33];
+    // P + 1 with P = round(p * 2^32): Q_K <= K (P + 1), so u >= K (P + 1)
+    // proves that none of K candidates is forced (cheap exact pre-check).
+    unsigned long long p_plus_1;
 };
 
 struct Geometry {
@@ -61,7 +64,9 @@ struct TileArgs {
 // Step kernel choice: automatic, direct register loads, or the bulk-copy ring
 // (cp.async.bulk into shared memory; falls back to direct when a row does not
 // fit a stage).  Automatic picks the ring when it gets >= 2 tiles per SM.
-enum StepKernel { kStepAuto = 0, kStepDirect = 1, kStepRing = 2 };
+// kStepRun: the ring kernel running many steps in one cooperative launch
+// (per-tile dependency counters instead of a launch per step).
+enum StepKernel { kStepAuto = 0, kStepDirect = 1, kStepRing = 2, kStepRun = 3 };
 
 // Launch one time step (motion, scattering, bounce-back, forcing).
 // `err` (device word, may be NULL) is set nonzero if a bounded wait gives up.
@@ -70,8 +75,20 @@ cudaError_t launch_step(const Geometry& g, const uint32_t* src, uint32_t* dst,
                         const ForcingTable& ft, Key2 key, uint64_t t, cudaStream_t stream,
                         unsigned int* err = nullptr, int kernel = kStepAuto);
 
-// The kernel launch_step(kernel = requested) runs: kStepDirect or kStepRing.
+// The kernel fhp_step uses for `requested`: kStepDirect, kStepRing or kStepRun
+// (launch_step itself runs kStepRing for kStepRun: one step per launch).
 int resolved_step_kernel(const Geometry& g, bool has_solid, int requested);
+
+// Tiles of the ring / multi-step kernels (0 if a row does not fit a stage);
+// the multi-step kernel needs that many counter words of scratch.
+int run_tiles(const Geometry& g, bool has_solid);
+
+// n >= 1 steps from buf0 (state at t0) in one cooperative launch; the result
+// is in buf0 if n is even, else in buf1.  `done` holds run_tiles() words of
+// scratch (zeroed by the call on the stream).
+cudaError_t launch_run(const Geometry& g, uint32_t* buf0, uint32_t* buf1, const uint32_t* solid,
+                       bool has_solid, bool force, const ForcingTable& ft, Key2 key, uint64_t t0,
+                       int nsteps, unsigned int* done, cudaStream_t stream, unsigned int* err);
 
 // Pack H x W node bytes (device) into 7 state planes + the solid plane.
 // Sets *device_any_solid to a nonzero value if any node is solid.

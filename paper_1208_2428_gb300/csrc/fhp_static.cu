@@ -63,6 +63,7 @@ fhp::ForcingTable thresholds(double p) {
     else P = (unsigned long long)std::nearbyint(scaled);
     fhp::ForcingTable ft;
     unsigned long long S = one;
+    ft.p_plus_1 = P + 1;
     ft.q[0] = 0;
     for (int g = 1; g <= 32; ++g) {
         S = (unsigned long long)(((unsigned __int128)S * (one - P)) >> 32);

@@ -16,11 +16,11 @@
 //   128-bit stores of the seven planes into the other ping-pong buffer.
 //
 // Two kernels share that per-quad code:
-//   fhp_step_tma_kernel    persistent CTAs walk tiles of R full rows; one
-//                          thread streams each tile's plane rows into a
-//                          3-stage shared-memory ring with cp.async.bulk
-//                          (completion on an mbarrier), so loads for the next
-//                          tiles are in flight while all threads compute;
+//   fhp_step_tma_kernel    persistent CTAs walk tiles of R full rows; a
+//                          producer warp streams each tile's plane rows into
+//                          a 3-stage shared-memory ring with cp.async.bulk
+//                          (completion on mbarriers), so loads for the next
+//                          tiles are in flight while 8 consumer warps compute;
 //   fhp_step_direct_kernel one quad per thread, operands loaded straight into
 //                          registers and neighbour words exchanged with
 //                          __shfl_sync (used when a row is too wide to stage).
@@ -35,7 +35,9 @@ namespace {
 
 constexpr unsigned kFull = 0xFFFFFFFFu;
 constexpr int kBlock = 256;             // direct kernel
-constexpr int kTmaThreads = 256;        // bulk-copy kernel
+constexpr int kConsumerWarps = 8;       // bulk-copy kernel: compute warps
+constexpr int kTmaThreads = (kConsumerWarps + 1) * 32;  // + one producer warp
+constexpr int kRunThreads = (kConsumerWarps + 2) * 32;  // + producer and publisher warps
 constexpr int kStages = 3;              // shared-memory ring depth
 constexpr int kStageBudget = 32 * 1024; // bytes per stage
 constexpr int kBarrierBytes = 128;      // mbarriers at the front of shared memory
@@ -64,15 +66,22 @@ __device__ __forceinline__ uint4 pull_right(uint4 v, uint32_t right, int m) {
                       __funnelshift_r(v.z, n2, 1), __funnelshift_r(v.w, right, 1));
 }
 
+// Where one step writes and which step it is (varies per step in the
+// multi-step kernel; the single-step kernels take it from StepArgs).
+struct StepVar {
+    uint32_t* dst;
+    uint32_t t_lo, t_hi;
+};
+
 // Scattering, bounce-back, forcing and the store of one quad whose movers
 // have already been pulled (n0..n5), with rest plane i6 and solid plane sd.
 template <bool SOLID, bool FORCE, bool RAGGED>
-__device__ __forceinline__ void finish_quad(const StepArgs& a, int q, int y, int m, uint4 n0, uint4 n1,
-                                            uint4 n2, uint4 n3, uint4 n4, uint4 n5, uint4 i6,
+__device__ __forceinline__ void finish_quad(const StepArgs& a, const StepVar& v, int q, int y, int m, uint4 n0,
+                                            uint4 n1, uint4 n2, uint4 n3, uint4 n4, uint4 n5, uint4 i6,
                                             uint4 sd, bool active) {
-    const uint4 chi = rng_block((uint32_t)q, (uint32_t)y, a.t_lo, a.t_hi, 0u, a.key);
+    const uint4 chi = rng_block((uint32_t)q, (uint32_t)y, v.t_lo, v.t_hi, 0u, a.key);
     uint4 gate = make_uint4(0u, 0u, 0u, 0u);
-    if (FORCE) gate = rng_block((uint32_t)q, (uint32_t)y, a.t_lo, a.t_hi, 1u, a.key);
+    if (FORCE) gate = rng_block((uint32_t)q, (uint32_t)y, v.t_lo, v.t_hi, 1u, a.key);
 
     uint4 o0, o1, o2, o3, o4, o5, o6;
 #define FHP_WORD(J, C)                                                                          \
@@ -82,9 +91,10 @@ __device__ __forceinline__ void finish_quad(const StepArgs& a, int q, int y, int
         if (FORCE) {                                                                            \
             const uint32_t cand = (SOLID ? ~sd.C : 0xFFFFFFFFu) & out.m5 & ~out.m2;             \
             const uint32_t u = gate.C;                                                          \
+            /* u >= Q_32 >= Q_K: none of the word's candidates is forced (common case) */       \
             if (cand != 0u && (unsigned long long)u < a.ft.q[32]) {                             \
                 const uint32_t f = forced_mask(cand, u, a.ft, [&](uint32_t d) {                 \
-                    return word_of(rng_block((uint32_t)q, (uint32_t)y, a.t_lo, a.t_hi, 1u + d,   \
+                    return word_of(rng_block((uint32_t)q, (uint32_t)y, v.t_lo, v.t_hi, 1u + d,   \
                                              a.key), J);                                        \
                 });                                                                             \
                 out.m5 ^= f;                                                                    \
@@ -108,7 +118,7 @@ __device__ __forceinline__ void finish_quad(const StepArgs& a, int q, int y, int
         o0.w = o1.w = o2.w = o3.w = o4.w = o5.w = o6.w = 0u;
     }
     const size_t pw = a.plane_words;
-    uint32_t* d = a.dst + (size_t)y * a.Pq + 4 * q;
+    uint32_t* d = v.dst + (size_t)y * a.Pq + 4 * q;
     st4(d + 0 * pw, o0);
     st4(d + 1 * pw, o1);
     st4(d + 2 * pw, o2);
@@ -174,8 +184,8 @@ __device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32
 // R rows of Pq words; staged row r of every slot feeds output row y0 + r, so
 // slots 3, 4 hold source rows y0 + r - 1 and slots 0, 1 rows y0 + r + 1.
 template <bool SOLID>
-__device__ void issue_tile(const StepArgs& a, const TileArgs& ta, int tile, uint32_t* stage,
-                           uint64_t* bar) {
+__device__ void issue_tile(const StepArgs& a, const TileArgs& ta, const uint32_t* src, int tile,
+                           uint32_t* stage, uint64_t* bar) {
     constexpr int NP = SOLID ? 8 : 7;
     const int y0 = tile * ta.R;
     const int rows = min(ta.R, a.H - y0);
@@ -183,7 +193,7 @@ __device__ void issue_tile(const StepArgs& a, const TileArgs& ta, int tile, uint
     mbar_arrive_expect_tx(bar, (uint32_t)NP * (uint32_t)rows * row_bytes);
 #pragma unroll
     for (int slot = 0; slot < NP; ++slot) {
-        const uint32_t* plane = slot < 7 ? a.src + (size_t)slot * a.plane_words : a.solid;
+        const uint32_t* plane = slot < 7 ? src + (size_t)slot * a.plane_words : a.solid;
         const int shift = (slot == 3 || slot == 4) ? -1 : (slot == 0 || slot == 1) ? 1 : 0;
         int r = 0;
         while (r < rows) {
@@ -199,8 +209,8 @@ __device__ void issue_tile(const StepArgs& a, const TileArgs& ta, int tile, uint
 }
 
 template <bool SOLID, bool FORCE, bool RAGGED>
-__device__ __forceinline__ void quad_from_stage(const StepArgs& a, const TileArgs& ta, const uint32_t* stage,
-                                                int r, int y, int q) {
+__device__ __forceinline__ void quad_from_stage(const StepArgs& a, const StepVar& v, const TileArgs& ta,
+                                                const uint32_t* stage, int r, int y, int q) {
     const int Pq = a.Pq, R = ta.R;
     const int w = 4 * q;
     const int m = RAGGED ? (q == a.nq - 1 ? a.Wq - w : 4) : 4;
@@ -232,12 +242,12 @@ __device__ __forceinline__ void quad_from_stage(const StepArgs& a, const TileArg
         n3 = i3;
         n1 = i1;
     }
-    finish_quad<SOLID, FORCE, RAGGED>(a, q, y, m, n0, n1, n2, n3, n4, n5, i6, sd, true);
+    finish_quad<SOLID, FORCE, RAGGED>(a, v, q, y, m, n0, n1, n2, n3, n4, n5, i6, sd, true);
 }
 
 template <bool SOLID, bool FORCE, bool RAGGED>
-__device__ __forceinline__ void compute_tile(const StepArgs& a, const TileArgs& ta, int tile,
-                                             const uint32_t* stage) {
+__device__ __forceinline__ void compute_tile(const StepArgs& a, const StepVar& v, const TileArgs& ta, int tile,
+                                             const uint32_t* stage, int tid, int nthreads) {
     const int y0 = tile * ta.R;
     const int rows = min(ta.R, a.H - y0);
     // Items ordered even local rows first, then odd ones, so that the row
@@ -245,20 +255,30 @@ __device__ __forceinline__ void compute_tile(const StepArgs& a, const TileArgs& 
     const int even_rows = (rows + 1) >> 1;
     const int even_items = even_rows * a.nq;
     const int items = rows * a.nq;
-    for (int it = threadIdx.x; it < items; it += blockDim.x) {
+    for (int it = tid; it < items; it += nthreads) {
         const int h = it >= even_items;
         const uint32_t j = (uint32_t)(h ? it - even_items : it);
         const int k = (int)(((unsigned long long)j * ta.nq_magic) >> 32);  // j / nq
         const int q = (int)j - k * a.nq;
         const int r = 2 * k + h;
-        quad_from_stage<SOLID, FORCE, RAGGED>(a, ta, stage, r, y0 + r, q);
+        quad_from_stage<SOLID, FORCE, RAGGED>(a, v, ta, stage, r, y0 + r, q);
     }
 }
 
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+// Warp-specialised ring: warp kConsumerWarps (the producer) streams the CTA's
+// tiles into kStages shared-memory stages; "full" barriers (one arrival plus
+// the copies' bytes) release a stage to the consumer warps, and "empty"
+// barriers (one arrival per consumer warp) hand it back.  No block-wide
+// barrier is taken after set-up, and every wait is bounded.
 template <bool SOLID, bool FORCE, bool RAGGED>
 __global__ void __launch_bounds__(kTmaThreads, 2) fhp_step_tma_kernel(const StepArgs a, const TileArgs ta) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw);
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw);
+    uint64_t* empty = full + kStages;
     uint32_t* stages = reinterpret_cast<uint32_t*>(smem_raw + kBarrierBytes);
     constexpr int NP = SOLID ? 8 : 7;
     const size_t stage_words = (size_t)NP * ta.R * a.Pq;
@@ -266,43 +286,241 @@ __global__ void __launch_bounds__(kTmaThreads, 2) fhp_step_tma_kernel(const Step
     const int count = (ta.ntiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
     auto tile_of = [&](int i) { return (int)blockIdx.x + i * (int)gridDim.x; };
     auto stage_of = [&](int i) { return stages + (size_t)(i % kStages) * stage_words; };
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < kStages; ++s) mbar_init(&bars[s], 1);
+        for (int s = 0; s < kStages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], kConsumerWarps);
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
-    int issued = 0;
-    if (threadIdx.x == 0) {
-        for (; issued < kStages && issued < count; ++issued)
-            issue_tile<SOLID>(a, ta, tile_of(issued), stage_of(issued), &bars[issued % kStages]);
-    }
-    int abort_from = -1;
-    if (count > 0) {
-        const bool ok = mbar_wait_bounded(&bars[0], 0u);
-        if (__syncthreads_or(!ok)) abort_from = 0;
-    }
-    for (int i = 0; abort_from < 0 && i < count; ++i) {
-        compute_tile<SOLID, FORCE, RAGGED>(a, ta, tile_of(i), stage_of(i));
+
+    if (warp == kConsumerWarps) {
+        if (lane != 0) return;
+        int i = 0;
         bool ok = true;
-        if (i + 1 < count) ok = mbar_wait_bounded(&bars[(i + 1) % kStages], (uint32_t)(((i + 1) / kStages) & 1));
-        // Everyone is done with stage i % kStages (and has seen tile i+1 land).
-        if (__syncthreads_or(!ok)) {
-            abort_from = i + 1;
-            break;
-        }
-        if (threadIdx.x == 0 && issued < count) {
+        for (; i < count; ++i) {
+            const int s = i % kStages;
+            if (i >= kStages && !mbar_wait_bounded(&empty[s], (uint32_t)(((i / kStages) - 1) & 1))) {
+                ok = false;
+                break;
+            }
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            issue_tile<SOLID>(a, ta, tile_of(issued), stage_of(issued), &bars[issued % kStages]);
-            ++issued;
+            issue_tile<SOLID>(a, ta, a.src, tile_of(i), stage_of(i), &full[s]);
         }
+        if (!ok && a.err) atomicOr(a.err, 1u);
+        // Never leave while copies into this CTA's shared memory may be in flight.
+        for (int k = (i > kStages ? i - kStages : 0); k < i; ++k)
+            (void)mbar_wait_bounded(&full[k % kStages], (uint32_t)((k / kStages) & 1));
+        return;
     }
-    if (abort_from >= 0 && threadIdx.x == 0) {
-        // A copy never completed: report it, and do not leave the CTA while
-        // copies into its shared memory may still be in flight.
-        if (a.err) atomicOr(a.err, 1u);
-        for (int k = abort_from; k < issued; ++k)
-            (void)mbar_wait_bounded(&bars[k % kStages], (uint32_t)((k / kStages) & 1));
+
+    const StepVar v{a.dst, a.t_lo, a.t_hi};
+    for (int i = 0; i < count; ++i) {
+        const int s = i % kStages;
+        if (!mbar_wait_bounded(&full[s], (uint32_t)((i / kStages) & 1))) {
+            if (lane == 0 && a.err) atomicOr(a.err, 1u);
+            return;
+        }
+        compute_tile<SOLID, FORCE, RAGGED>(a, v, ta, tile_of(i), stage_of(i), (int)threadIdx.x,
+                                           kConsumerWarps * 32);
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[s]);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Multi-step kernel: all n steps in one cooperative launch.  Tiles of step s
+// depend only on the three tiles of step s-1 that hold their source rows
+// (tile j reads rows y0-1 .. y0+R of the previous state), so instead of a
+// grid-wide barrier per step every tile carries a counter of consumer warps
+// that finished it (bumped by a publisher warp after a GPU-scope fence, so
+// neither the compute warps nor stage reuse wait on a fence); the producer of
+// (s, j) waits (bounded) until tiles j-1, j, j+1 reached kConsumerWarps * s
+// before streaming its inputs.  That also
+// makes the write of (s, j) safe: the three tiles that read the old rows of j
+// (at step s-1) have finished.  All CTAs are co-resident (cooperative launch)
+// and each walks its items in step order, so every wait is for an item that
+// is already running or finished.
+// ---------------------------------------------------------------------------
+struct RunArgs {
+    uint32_t* buf0;          // state S_{t0} (also StepArgs::src)
+    uint32_t* buf1;          // the other buffer (StepArgs::dst)
+    unsigned int* done;      // per-tile finished-warp counters, zero at launch
+    int nsteps;
+    unsigned long long t0;
+};
+
+__device__ __forceinline__ unsigned int ld_relaxed_gpu(const unsigned int* p) {
+    unsigned int v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Wait until the counters of tiles a, b (and c if check_c) reach `target`.
+// The loads are relaxed so that they are in flight together; one acquire
+// fence after they all pass orders the later reads of the tiles' rows.
+// Gives up (false) after kWaitLimitNs.
+__device__ __noinline__ bool wait_tiles(const unsigned int* done, int ta_, int tb, int tc, bool check_c,
+                                        unsigned int target) {
+    unsigned long long start = 0;
+    for (;;) {
+        const unsigned int va = ld_relaxed_gpu(done + ta_);
+        const unsigned int vb = ld_relaxed_gpu(done + tb);
+        const unsigned int vc = check_c ? ld_relaxed_gpu(done + tc) : target;
+        if (va >= target && vb >= target && vc >= target) {
+            asm volatile("fence.acq_rel.gpu;" ::: "memory");
+            return true;
+        }
+        const unsigned long long now = global_ns();
+        if (start == 0) start = now;
+        else if (now - start > kWaitLimitNs) return false;
+        __nanosleep(32);
+    }
+}
+
+__device__ __forceinline__ void st_release_cta_shared(unsigned int* p, unsigned int v) {
+    asm volatile("st.release.cta.shared::cta.u32 [%0], %1;" ::"r"(smem_addr(p)), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ unsigned int ld_acquire_cta_shared(const unsigned int* p) {
+    unsigned int v;
+    asm volatile("ld.acquire.cta.shared::cta.u32 %0, [%1];" : "=r"(v) : "r"(smem_addr(p)) : "memory");
+    return v;
+}
+
+template <bool SOLID, bool FORCE, bool RAGGED>
+__global__ void __launch_bounds__(kRunThreads, 2) fhp_run_kernel(const StepArgs a, const TileArgs ta,
+                                                                 const RunArgs ra) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw);
+    uint64_t* empty = full + kStages;  // all consumer warps finished the stage's tile
+    // warp_done[w]: number of items consumer warp w has finished (written
+    // with release, read by the publisher with acquire).
+    unsigned int* warp_done = reinterpret_cast<unsigned int*>(empty + kStages);
+    uint32_t* stages = reinterpret_cast<uint32_t*>(smem_raw + kBarrierBytes);
+    constexpr int NP = SOLID ? 8 : 7;
+    const size_t stage_words = (size_t)NP * ta.R * a.Pq;
+    const int count = (ta.ntiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], kConsumerWarps);
+        }
+        for (int w = 0; w < kConsumerWarps; ++w) warp_done[w] = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+
+    if (warp == kConsumerWarps + 1) {
+        // Publisher: every item all consumer warps have finished gets its
+        // tile counter bumped after one GPU-scope fence; when it falls
+        // behind, one fence covers several items.  The compute warps never
+        // wait on a fence and stage reuse never waits on the publisher.
+        if (lane != 0) return;
+        const long long total = (long long)count * ra.nsteps;
+        long long published = 0;
+        int i_next = 0;  // tile index (within this CTA) of item `published`
+        unsigned long long start = 0;
+        while (published < total) {
+            unsigned int m = 0xFFFFFFFFu;
+            for (int w = 0; w < kConsumerWarps; ++w) m = min(m, ld_acquire_cta_shared(&warp_done[w]));
+            if ((long long)m > published) {
+                asm volatile("fence.proxy.async.global;" ::: "memory");
+                asm volatile("fence.acq_rel.gpu;" ::: "memory");
+                for (; published < (long long)m; ++published) {
+                    atomicAdd(&ra.done[(int)blockIdx.x + i_next * (int)gridDim.x], (unsigned int)kConsumerWarps);
+                    if (++i_next == count) i_next = 0;
+                }
+                start = 0;
+                continue;
+            }
+            const unsigned long long now = global_ns();
+            if (start == 0) start = now;
+            else if (now - start > kWaitLimitNs) {
+                if (a.err) atomicOr(a.err, 1u);
+                return;
+            }
+            __nanosleep(64);
+        }
+        return;
+    }
+
+    if (warp == kConsumerWarps) {
+        if (lane != 0) return;
+        // Item k = s * count + i goes to stage k % kStages; its "full" phase
+        // parity is (k / kStages) & 1, and it may reuse the stage once the
+        // "empty" phase of item k - kStages (parity flipped) has completed.
+        long long k = 0;
+        int st = 0;
+        uint32_t par = 0;
+        bool ok = true;
+        for (int s = 0; ok && s < ra.nsteps; ++s) {
+            const uint32_t* src = (s & 1) ? ra.buf1 : ra.buf0;
+            const unsigned int target = (unsigned int)kConsumerWarps * (unsigned int)s;
+            for (int i = 0; i < count; ++i) {
+                const int tile = (int)blockIdx.x + i * (int)gridDim.x;
+                if (k >= kStages && !mbar_wait_bounded(&empty[st], par ^ 1u)) {
+                    ok = false;
+                    break;
+                }
+                if (s > 0) {
+                    // Tiles prev, tile, next of step s - 1 hold the source rows.
+                    const int prev = tile == 0 ? ta.ntiles - 1 : tile - 1;
+                    const int next = tile == ta.ntiles - 1 ? 0 : tile + 1;
+                    if (!wait_tiles(ra.done, prev, next, tile, true, target)) {
+                        ok = false;
+                        break;
+                    }
+                    // The rows were written through the generic proxy by other
+                    // warps and CTAs; the bulk copy reads them through the
+                    // async proxy.
+                    asm volatile("fence.proxy.async.global;" ::: "memory");
+                }
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                issue_tile<SOLID>(a, ta, src, tile, stages + (size_t)st * stage_words, &full[st]);
+                ++k;
+                if (++st == kStages) {
+                    st = 0;
+                    par ^= 1u;
+                }
+            }
+        }
+        if (!ok && a.err) atomicOr(a.err, 1u);
+        // Never leave while copies into this CTA's shared memory may be in flight.
+        for (long long j = (k > kStages ? k - kStages : 0); j < k; ++j)
+            (void)mbar_wait_bounded(&full[j % kStages], (uint32_t)((j / kStages) & 1));
+        return;
+    }
+
+    int st = 0;
+    uint32_t par = 0;
+    unsigned int finished = 0;
+    for (int s = 0; s < ra.nsteps; ++s) {
+        const unsigned long long t = ra.t0 + (unsigned long long)s;
+        const StepVar v{(s & 1) ? ra.buf0 : ra.buf1, (uint32_t)t, (uint32_t)(t >> 32)};
+        for (int i = 0; i < count; ++i) {
+            const int tile = (int)blockIdx.x + i * (int)gridDim.x;
+            if (!mbar_wait_bounded(&full[st], par)) {
+                if (lane == 0 && a.err) atomicOr(a.err, 1u);
+                return;
+            }
+            compute_tile<SOLID, FORCE, RAGGED>(a, v, ta, tile, stages + (size_t)st * stage_words,
+                                               (int)threadIdx.x, kConsumerWarps * 32);
+            __syncwarp();
+            if (lane == 0) {
+                mbar_arrive(&empty[st]);                        // the stage may be refilled
+                st_release_cta_shared(&warp_done[warp], ++finished);  // this warp's rows are written
+            }
+            if (++st == kStages) {
+                st = 0;
+                par ^= 1u;
+            }
+        }
     }
 }
 
@@ -404,11 +622,12 @@ __device__ __forceinline__ void direct_quad(const StepArgs& a, const Lane& L) {
         n3 = i3;
         n1 = i1;
     }
-    finish_quad<SOLID, FORCE, RAGGED>(a, L.q, y, m, n0, n1, n2, n3, n4, n5, i6, sd, L.active);
+    const StepVar v{a.dst, a.t_lo, a.t_hi};
+    finish_quad<SOLID, FORCE, RAGGED>(a, v, L.q, y, m, n0, n1, n2, n3, n4, n5, i6, sd, L.active);
 }
 
 template <bool SOLID, bool FORCE, bool RAGGED>
-__global__ void __launch_bounds__(kBlock) fhp_step_direct_kernel(const StepArgs a) {
+__global__ void __launch_bounds__(kBlock, 4) fhp_step_direct_kernel(const StepArgs a) {
     const Lane L = map_lane(a);
     if (L.y & 1) direct_quad<SOLID, FORCE, RAGGED, true>(a, L);
     else direct_quad<SOLID, FORCE, RAGGED, false>(a, L);
@@ -434,6 +653,8 @@ struct DeviceInfo {
     int sms = 0;
     int tma_blocks_per_sm[8] = {};  // per kernel variant (solid, force, ragged)
     bool configured[8] = {};
+    int run_blocks_per_sm[8] = {};
+    bool run_configured[8] = {};
 };
 std::mutex g_dev_mutex;
 DeviceInfo g_dev[64];
@@ -470,6 +691,55 @@ cudaError_t launch_tma_variant(const StepArgs& a, const TileArgs& ta, size_t sme
     const int grid = min(ta.ntiles, blocks_per_sm * sms);
     kernel<<<grid, kTmaThreads, smem, s>>>(a, ta);
     return cudaGetLastError();
+}
+
+template <bool SOLID, bool FORCE, bool RAGGED>
+cudaError_t launch_run_variant(const StepArgs& a, const TileArgs& ta, const RunArgs& ra, size_t smem,
+                               cudaStream_t s) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    const int variant = (SOLID ? 4 : 0) | (FORCE ? 2 : 0) | (RAGGED ? 1 : 0);
+    auto kernel = fhp_run_kernel<SOLID, FORCE, RAGGED>;
+    int blocks_per_sm, sms;
+    {
+        std::lock_guard<std::mutex> lock(g_dev_mutex);
+        DeviceInfo& d = g_dev[dev];
+        if (!d.sms) {
+            e = cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev);
+            if (e != cudaSuccess) return e;
+        }
+        if (!d.run_configured[variant]) {
+            const int max_smem = kBarrierBytes + kStages * kStageBudget;
+            e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+            if (e != cudaSuccess) return e;
+            int n = 0;
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, kRunThreads, max_smem);
+            if (e != cudaSuccess) return e;
+            d.run_blocks_per_sm[variant] = n > 0 ? n : 1;
+            d.run_configured[variant] = true;
+        }
+        blocks_per_sm = d.run_blocks_per_sm[variant];
+        sms = d.sms;
+    }
+    // Every CTA must be resident at once (they wait on each other's tiles):
+    // a cooperative launch with at most the co-resident number of CTAs.
+    const int grid = min(ta.ntiles, blocks_per_sm * sms);
+    StepArgs a_copy = a;
+    TileArgs ta_copy = ta;
+    RunArgs ra_copy = ra;
+    void* args[] = {&a_copy, &ta_copy, &ra_copy};
+    e = cudaLaunchCooperativeKernel((const void*)kernel, dim3(grid), dim3(kRunThreads), args, smem, s);
+    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+}
+
+template <bool SOLID, bool FORCE>
+cudaError_t launch_run(const StepArgs& a, const TileArgs& ta, const RunArgs& ra, size_t smem, bool ragged,
+                       cudaStream_t s) {
+    return ragged ? launch_run_variant<SOLID, FORCE, true>(a, ta, ra, smem, s)
+                  : launch_run_variant<SOLID, FORCE, false>(a, ta, ra, smem, s);
 }
 
 template <bool SOLID, bool FORCE>
@@ -520,7 +790,7 @@ Geometry make_geometry(int W, int H) {
 int resolved_step_kernel(const Geometry& g, bool has_solid, int requested) {
     const int R = tile_rows(g, has_solid);
     if (R == 0 || requested == kStepDirect) return kStepDirect;
-    if (requested == kStepRing) return kStepRing;
+    if (requested == kStepRing || requested == kStepRun) return requested;
     int dev = 0, sms = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return kStepDirect;
     {
@@ -530,8 +800,58 @@ int resolved_step_kernel(const Geometry& g, bool has_solid, int requested) {
             return kStepDirect;
         sms = g_dev[dev].sms;
     }
+    // Few tiles per CTA and step: launch gaps and per-step pipeline refills
+    // dominate, so run all steps in one launch.  Many tiles per CTA: the
+    // per-step overhead is small and the single-step ring streams best.
     const int ntiles = (g.H + R - 1) / R;
-    return ntiles >= 2 * sms ? kStepRing : kStepDirect;
+    if (ntiles < 2 * sms) return kStepDirect;
+    return ntiles <= 12 * 2 * sms ? kStepRun : kStepRing;
+}
+
+int run_tiles(const Geometry& g, bool has_solid) {
+    const int R = tile_rows(g, has_solid);
+    return R > 0 ? (g.H + R - 1) / R : 0;
+}
+
+cudaError_t launch_run(const Geometry& g, uint32_t* buf0, uint32_t* buf1, const uint32_t* solid,
+                       bool has_solid, bool force, const ForcingTable& ft, Key2 key, uint64_t t0,
+                       int nsteps, unsigned int* done, cudaStream_t stream, unsigned int* err) {
+    const int R = tile_rows(g, has_solid);
+    if (R == 0 || nsteps <= 0) return cudaErrorInvalidValue;
+    StepArgs a;
+    a.src = buf0;
+    a.dst = buf1;
+    a.solid = solid;
+    a.plane_words = g.plane_words;
+    a.H = g.H;
+    a.Wq = g.Wq;
+    a.nq = g.nq;
+    a.Pq = g.Pq;
+    a.rows_per_warp = a.groups_per_parity = a.warps_per_row = 1;
+    a.key = key;
+    a.t_lo = (uint32_t)t0;
+    a.t_hi = (uint32_t)(t0 >> 32);
+    a.err = err;
+    a.ft = ft;
+    TileArgs ta;
+    ta.R = R;
+    ta.ntiles = (g.H + R - 1) / R;
+    ta.nq_magic = ((1ull << 32) + g.nq - 1) / g.nq;
+    RunArgs ra;
+    ra.buf0 = buf0;
+    ra.buf1 = buf1;
+    ra.done = done;
+    ra.nsteps = nsteps;
+    ra.t0 = t0;
+    cudaError_t e = cudaMemsetAsync(done, 0, (size_t)ta.ntiles * sizeof(unsigned int), stream);
+    if (e != cudaSuccess) return e;
+    const size_t smem = kBarrierBytes + (size_t)kStages * (has_solid ? 8 : 7) * R * g.Pq * 4;
+    const bool ragged = (g.Wq % 4) != 0;
+    if (has_solid)
+        return force ? launch_run<true, true>(a, ta, ra, smem, ragged, stream)
+                     : launch_run<true, false>(a, ta, ra, smem, ragged, stream);
+    return force ? launch_run<false, true>(a, ta, ra, smem, ragged, stream)
+                 : launch_run<false, false>(a, ta, ra, smem, ragged, stream);
 }
 
 cudaError_t launch_step(const Geometry& g, const uint32_t* src, uint32_t* dst,
@@ -554,7 +874,7 @@ cudaError_t launch_step(const Geometry& g, const uint32_t* src, uint32_t* dst,
     a.ft = ft;
     const bool ragged = (g.Wq % 4) != 0;
     const int R = tile_rows(g, has_solid);
-    if (resolved_step_kernel(g, has_solid, kernel) == kStepRing) {
+    if (resolved_step_kernel(g, has_solid, kernel) != kStepDirect) {
         TileArgs ta;
         ta.R = R;
         ta.ntiles = (g.H + R - 1) / R;

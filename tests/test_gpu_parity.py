@@ -64,7 +64,7 @@ SHAPES = [
 ]
 
 
-KERNELS = [1, 2]   # direct register loads; bulk-copy shared-memory ring
+KERNELS = [1, 2, 3]   # direct register loads; bulk-copy ring; multi-step ring (one launch)
 
 
 @pytest.mark.parametrize("kernel", KERNELS)
@@ -99,14 +99,16 @@ def test_parity_empty_and_full(fhp_mod, oracle_mod, kernel):
         assert_same(gpu_run(fhp_mod, s0, 3, 0, 4, 0.5, kernel=kernel), want, "all solid")
 
 
-@pytest.mark.parametrize("W,H", [(256, 2048), (4096, 1024), (2048, 512), (96, 4096)])
-def test_parity_ring_many_tiles(fhp_mod, oracle_mod, W, H):
-    """Shapes where the ring kernel walks many tiles per CTA (pipeline wrap-around)."""
+@pytest.mark.parametrize("kernel", [2, 3])
+@pytest.mark.parametrize("W,H", [(256, 2048), (4096, 1024), (2048, 512), (96, 4096), (4128, 6000)])
+def test_parity_ring_many_tiles(fhp_mod, oracle_mod, W, H, kernel):
+    """Shapes where the ring kernels walk many tiles per CTA (pipeline wrap-around,
+    dependency waits across step boundaries for the multi-step kernel)."""
     seed = W + H
     s0 = workloads.bernoulli_lattice(W, H, 0.3, seed, workloads.cylinder_mask(W, H))
-    want, _ = oracle_mod.run(s0, seed, 0, 6, 0.01)
-    got = gpu_run(fhp_mod, s0, seed, 0, 6, 0.01, kernel=2)
-    assert_same(got, want, f"ring {W}x{H}")
+    want, _ = oracle_mod.run(s0, seed, 0, 7, 0.01)
+    got = gpu_run(fhp_mod, s0, seed, 0, 7, 0.01, kernel=kernel)
+    assert_same(got, want, f"kernel {kernel} {W}x{H}")
 
 
 def test_parity_large_step_counter(fhp_mod, oracle_mod):
@@ -166,10 +168,11 @@ def test_cylinder_full_size(fhp_mod, oracle_mod):
     want, ev = oracle_mod.run(s0, job.seed, 0, n, job.p)
     with fhp_mod.Lattice(job.W, job.H, seed=job.seed, forcing_p=job.p) as lat:
         lat.set_state(s0)
-        assert lat.step_kernel == 2      # the ring kernel is what the benchmark times
+        assert lat.step_kernel == 3      # the multi-step ring kernel is what the benchmark times
         lat.step(n)
         assert_same(lat.get_state(), want, "cylinder 16384x4096")
-    assert_same(gpu_run(fhp_mod, s0, job.seed, 0, n, job.p, kernel=1), want, "cylinder, direct kernel")
+    for k in (1, 2):
+        assert_same(gpu_run(fhp_mod, s0, job.seed, 0, n, job.p, kernel=k), want, f"cylinder, kernel {k}")
 
 
 def test_paper_size_lattice(fhp_mod, oracle_mod):
