@@ -142,7 +142,13 @@ FHP_API int fhp_set_time(fhp_lattice* lattice, int64_t t);
 FHP_API int fhp_set_forcing(fhp_lattice* lattice, double p);
 
 /* Number of steps fused into one kernel pass (temporal blocking): 1, 2, 4
- * or 8.  Results are identical for every value.  Default 1. */
+ * or 8.  With k > 1, fhp_step runs passes that stage a tile of the lattice
+ * plus a k-row (and one 128-node) halo in shared memory and apply k steps
+ * there before writing the tile back, so HBM is read and written once per k
+ * steps; leftover steps (n mod k) and lattices the blocked kernel does not
+ * support (W not a multiple of 128, fewer than 512 nodes per row, or
+ * H < 2k + 2) use the single-step kernels.  Results are identical for every
+ * value.  Default 1. */
 FHP_API int fhp_set_temporal_block(fhp_lattice* lattice, int32_t k);
 
 /* Step kernel used by fhp_step: 0 = automatic (default), 1 = direct (one

@@ -295,6 +295,19 @@ int fhp_step(fhp_lattice* h, int64_t n) {
     if (n > kMaxTime - h->t) return fail(h, FHP_EINVAL, "step counter would pass 2^48");
     DeviceGuard dg(h->device);
     const fhp::Key2 key{(uint32_t)h->seed, (uint32_t)(h->seed >> 32)};
+    if (h->k_block > 1 && fhp::block_supported(h->g, h->k_block)) {
+        // Temporal blocking: passes of k steps; the remainder one step at a time.
+        const int k = h->k_block;
+        while (n >= k) {
+            cudaError_t e = fhp::launch_block(h->g, h->buf[h->cur], h->buf[h->cur ^ 1], h->solid, h->has_solid,
+                                              h->force, h->ft, key, (uint64_t)h->t, k, h->stream, h->flags + 1);
+            if (e != cudaSuccess) return cuda_fail(h, e, "launching the temporally blocked kernel");
+            ++h->launches;
+            h->cur ^= 1;
+            h->t += k;
+            n -= k;
+        }
+    }
     if (n >= 2 && fhp::resolved_step_kernel(h->g, h->has_solid, h->step_kernel) == fhp::kStepRun) {
         // All n steps in cooperative launches of up to 2^24 steps each.
         int64_t left = n;

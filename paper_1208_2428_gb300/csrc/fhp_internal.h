@@ -90,6 +90,14 @@ cudaError_t launch_run(const Geometry& g, uint32_t* buf0, uint32_t* buf1, const 
                        bool has_solid, bool force, const ForcingTable& ft, Key2 key, uint64_t t0,
                        int nsteps, unsigned int* done, cudaStream_t stream, unsigned int* err);
 
+// Temporal blocking: k (2, 4 or 8) steps from src (state at t0) to dst in one
+// pass.  Supported when rows are whole quads (W multiple of 128), there are
+// at least 4 quads per row and H >= 2k + 2.
+bool block_supported(const Geometry& g, int k);
+cudaError_t launch_block(const Geometry& g, const uint32_t* src, uint32_t* dst, const uint32_t* solid,
+                         bool has_solid, bool force, const ForcingTable& ft, Key2 key, uint64_t t0, int k,
+                         cudaStream_t stream, unsigned int* err);
+
 // Pack H x W node bytes (device) into 7 state planes + the solid plane.
 // Sets *device_any_solid to a nonzero value if any node is solid.
 cudaError_t launch_pack(const Geometry& g, const uint8_t* bytes, uint32_t* state,

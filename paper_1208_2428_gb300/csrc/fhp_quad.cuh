@@ -1,0 +1,166 @@
+// fhp_quad.cuh -- per-quad building blocks shared by the step kernels
+// (fhp_step.cu) and the temporally blocked kernel (fhp_block.cu): 128-bit
+// plane access, the one-node shifts of the motion step, scattering plus
+// forcing of one quad (4 words = 128 nodes), and the mbarrier / bulk-copy
+// helpers (inline PTX) of the shared-memory pipelines.
+#pragma once
+
+#include "fhp_device.cuh"
+#include "fhp_internal.h"
+
+namespace fhp {
+namespace {
+
+constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // 2 s bound on any wait
+
+__device__ __forceinline__ uint4 ld4(const uint32_t* p) { return *reinterpret_cast<const uint4*>(p); }
+__device__ __forceinline__ void st4(uint32_t* p, uint4 v) { *reinterpret_cast<uint4*>(p) = v; }
+
+// New bit x takes old bit x-1; `left` is the word left of the quad.
+__device__ __forceinline__ uint4 pull_left(uint4 v, uint32_t left) {
+    return make_uint4(__funnelshift_l(left, v.x, 1), __funnelshift_l(v.x, v.y, 1),
+                      __funnelshift_l(v.y, v.z, 1), __funnelshift_l(v.z, v.w, 1));
+}
+
+// New bit x takes old bit x+1; `right` is the word right of the quad's last
+// valid word (m valid words; the rest of a ragged last quad is padding).
+template <bool RAGGED>
+__device__ __forceinline__ uint4 pull_right(uint4 v, uint32_t right, int m) {
+    uint32_t n0 = v.y, n1 = v.z, n2 = v.w;
+    if (RAGGED) {
+        if (m == 1) n0 = right;
+        if (m == 2) n1 = right;
+        if (m == 3) n2 = right;
+    }
+    return make_uint4(__funnelshift_r(v.x, n0, 1), __funnelshift_r(v.y, n1, 1),
+                      __funnelshift_r(v.z, n2, 1), __funnelshift_r(v.w, right, 1));
+}
+
+// Where one step writes and which step it is (varies per step in the
+// multi-step kernel; the single-step kernels take it from StepArgs).
+struct StepVar {
+    uint32_t* dst;
+    uint32_t t_lo, t_hi;
+};
+
+// Scattering, bounce-back and forcing of one quad (global quad index q of
+// row y at step v.t) whose movers have already been pulled (n0..n5), with
+// rest plane i6 and solid plane sd; the seven result planes go to o[0..6].
+template <bool SOLID, bool FORCE>
+__device__ __forceinline__ void collide_quad(const StepArgs& a, const StepVar& v, int q, int y, uint4 n0, uint4 n1,
+                                             uint4 n2, uint4 n3, uint4 n4, uint4 n5, uint4 i6, uint4 sd,
+                                             uint4 (&o)[7]) {
+    const uint4 chi = rng_block((uint32_t)q, (uint32_t)y, v.t_lo, v.t_hi, 0u, a.key);
+    uint4 gate = make_uint4(0u, 0u, 0u, 0u);
+    if (FORCE) gate = rng_block((uint32_t)q, (uint32_t)y, v.t_lo, v.t_hi, 1u, a.key);
+
+#define FHP_WORD(J, C)                                                                          \
+    {                                                                                           \
+        Planes7 in{n0.C, n1.C, n2.C, n3.C, n4.C, n5.C, i6.C};                                   \
+        Planes7 out = scatter(in, SOLID ? sd.C : 0u, chi.C);                                    \
+        if (FORCE) {                                                                            \
+            const uint32_t cand = (SOLID ? ~sd.C : 0xFFFFFFFFu) & out.m5 & ~out.m2;             \
+            const uint32_t u = gate.C;                                                          \
+            /* u >= Q_32 >= Q_K: none of the word's candidates is forced (common case) */       \
+            if (cand != 0u && (unsigned long long)u < a.ft.q[32]) {                             \
+                const uint32_t f = forced_mask(cand, u, a.ft, [&](uint32_t d) {                 \
+                    return word_of(rng_block((uint32_t)q, (uint32_t)y, v.t_lo, v.t_hi, 1u + d,   \
+                                             a.key), J);                                        \
+                });                                                                             \
+                out.m5 ^= f;                                                                    \
+                out.m2 ^= f;                                                                    \
+            }                                                                                   \
+        }                                                                                       \
+        o[0].C = out.m0; o[1].C = out.m1; o[2].C = out.m2; o[3].C = out.m3;                     \
+        o[4].C = out.m4; o[5].C = out.m5; o[6].C = out.rest;                                    \
+    }
+    FHP_WORD(0, x)
+    FHP_WORD(1, y)
+    FHP_WORD(2, z)
+    FHP_WORD(3, w)
+#undef FHP_WORD
+
+}
+
+// Store a quad's seven result planes to global memory (the padding words of
+// a ragged last quad are written as zero).
+template <bool RAGGED>
+__device__ __forceinline__ void store_quad(const StepArgs& a, uint32_t* dst, int q, int y, int m, uint4 (&o)[7]) {
+    if (RAGGED && m < 4) {
+#pragma unroll
+        for (int k = 0; k < 7; ++k) {
+            if (m < 2) o[k].y = 0u;
+            if (m < 3) o[k].z = 0u;
+            o[k].w = 0u;
+        }
+    }
+    const size_t pw = a.plane_words;
+    uint32_t* d = dst + (size_t)y * a.Pq + 4 * q;
+#pragma unroll
+    for (int k = 0; k < 7; ++k) st4(d + k * pw, o[k]);
+}
+
+// Collide and store one quad.
+template <bool SOLID, bool FORCE, bool RAGGED>
+__device__ __forceinline__ void finish_quad(const StepArgs& a, const StepVar& v, int q, int y, int m, uint4 n0,
+                                            uint4 n1, uint4 n2, uint4 n3, uint4 n4, uint4 n5, uint4 i6,
+                                            uint4 sd, bool active) {
+    uint4 o[7];
+    collide_quad<SOLID, FORCE>(a, v, q, y, n0, n1, n2, n3, n4, n5, i6, sd, o);
+    if (active) store_quad<RAGGED>(a, v.dst, q, y, m, o);
+}
+
+// ---------------------------------------------------------------------------
+// Bulk-copy kernel: mbarrier / cp.async.bulk helpers (inline PTX).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Wait for phase `parity` of `bar`; gives up (returns false) after kWaitLimitNs.
+__device__ __noinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long start = global_ns();
+    for (;;) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (global_ns() - start > kWaitLimitNs) return false;
+    }
+}
+
+__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+
+}  // namespace
+}  // namespace fhp

@@ -29,6 +29,7 @@
 
 #include "fhp_device.cuh"
 #include "fhp_internal.h"
+#include "fhp_quad.cuh"
 
 namespace fhp {
 namespace {
@@ -41,144 +42,6 @@ constexpr int kRunThreads = (kConsumerWarps + 2) * 32;  // + producer and publis
 constexpr int kStages = 3;              // shared-memory ring depth
 constexpr int kStageBudget = 32 * 1024; // bytes per stage
 constexpr int kBarrierBytes = 128;      // mbarriers at the front of shared memory
-constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // 2 s bound on any wait
-
-__device__ __forceinline__ uint4 ld4(const uint32_t* p) { return *reinterpret_cast<const uint4*>(p); }
-__device__ __forceinline__ void st4(uint32_t* p, uint4 v) { *reinterpret_cast<uint4*>(p) = v; }
-
-// New bit x takes old bit x-1; `left` is the word left of the quad.
-__device__ __forceinline__ uint4 pull_left(uint4 v, uint32_t left) {
-    return make_uint4(__funnelshift_l(left, v.x, 1), __funnelshift_l(v.x, v.y, 1),
-                      __funnelshift_l(v.y, v.z, 1), __funnelshift_l(v.z, v.w, 1));
-}
-
-// New bit x takes old bit x+1; `right` is the word right of the quad's last
-// valid word (m valid words; the rest of a ragged last quad is padding).
-template <bool RAGGED>
-__device__ __forceinline__ uint4 pull_right(uint4 v, uint32_t right, int m) {
-    uint32_t n0 = v.y, n1 = v.z, n2 = v.w;
-    if (RAGGED) {
-        if (m == 1) n0 = right;
-        if (m == 2) n1 = right;
-        if (m == 3) n2 = right;
-    }
-    return make_uint4(__funnelshift_r(v.x, n0, 1), __funnelshift_r(v.y, n1, 1),
-                      __funnelshift_r(v.z, n2, 1), __funnelshift_r(v.w, right, 1));
-}
-
-// Where one step writes and which step it is (varies per step in the
-// multi-step kernel; the single-step kernels take it from StepArgs).
-struct StepVar {
-    uint32_t* dst;
-    uint32_t t_lo, t_hi;
-};
-
-// Scattering, bounce-back, forcing and the store of one quad whose movers
-// have already been pulled (n0..n5), with rest plane i6 and solid plane sd.
-template <bool SOLID, bool FORCE, bool RAGGED>
-__device__ __forceinline__ void finish_quad(const StepArgs& a, const StepVar& v, int q, int y, int m, uint4 n0,
-                                            uint4 n1, uint4 n2, uint4 n3, uint4 n4, uint4 n5, uint4 i6,
-                                            uint4 sd, bool active) {
-    const uint4 chi = rng_block((uint32_t)q, (uint32_t)y, v.t_lo, v.t_hi, 0u, a.key);
-    uint4 gate = make_uint4(0u, 0u, 0u, 0u);
-    if (FORCE) gate = rng_block((uint32_t)q, (uint32_t)y, v.t_lo, v.t_hi, 1u, a.key);
-
-    uint4 o0, o1, o2, o3, o4, o5, o6;
-#define FHP_WORD(J, C)                                                                          \
-    {                                                                                           \
-        Planes7 in{n0.C, n1.C, n2.C, n3.C, n4.C, n5.C, i6.C};                                   \
-        Planes7 out = scatter(in, SOLID ? sd.C : 0u, chi.C);                                    \
-        if (FORCE) {                                                                            \
-            const uint32_t cand = (SOLID ? ~sd.C : 0xFFFFFFFFu) & out.m5 & ~out.m2;             \
-            const uint32_t u = gate.C;                                                          \
-            /* u >= Q_32 >= Q_K: none of the word's candidates is forced (common case) */       \
-            if (cand != 0u && (unsigned long long)u < a.ft.q[32]) {                             \
-                const uint32_t f = forced_mask(cand, u, a.ft, [&](uint32_t d) {                 \
-                    return word_of(rng_block((uint32_t)q, (uint32_t)y, v.t_lo, v.t_hi, 1u + d,   \
-                                             a.key), J);                                        \
-                });                                                                             \
-                out.m5 ^= f;                                                                    \
-                out.m2 ^= f;                                                                    \
-            }                                                                                   \
-        }                                                                                       \
-        o0.C = out.m0; o1.C = out.m1; o2.C = out.m2; o3.C = out.m3;                             \
-        o4.C = out.m4; o5.C = out.m5; o6.C = out.rest;                                          \
-    }
-    FHP_WORD(0, x)
-    FHP_WORD(1, y)
-    FHP_WORD(2, z)
-    FHP_WORD(3, w)
-#undef FHP_WORD
-
-    if (!active) return;
-    if (RAGGED && m < 4) {
-        // Keep the padding words of the last quad zero.
-        if (m < 2) { o0.y = o1.y = o2.y = o3.y = o4.y = o5.y = o6.y = 0u; }
-        if (m < 3) { o0.z = o1.z = o2.z = o3.z = o4.z = o5.z = o6.z = 0u; }
-        o0.w = o1.w = o2.w = o3.w = o4.w = o5.w = o6.w = 0u;
-    }
-    const size_t pw = a.plane_words;
-    uint32_t* d = v.dst + (size_t)y * a.Pq + 4 * q;
-    st4(d + 0 * pw, o0);
-    st4(d + 1 * pw, o1);
-    st4(d + 2 * pw, o2);
-    st4(d + 3 * pw, o3);
-    st4(d + 4 * pw, o4);
-    st4(d + 5 * pw, o5);
-    st4(d + 6 * pw, o6);
-}
-
-// ---------------------------------------------------------------------------
-// Bulk-copy kernel: mbarrier / cp.async.bulk helpers (inline PTX).
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ uint32_t smem_addr(const void* p) {
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
-                 : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
-    uint32_t done;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(done)
-        : "r"(smem_addr(bar)), "r"(parity)
-        : "memory");
-    return done != 0;
-}
-
-__device__ __forceinline__ unsigned long long global_ns() {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-// Wait for phase `parity` of `bar`; gives up (returns false) after kWaitLimitNs.
-__device__ __noinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
-    if (mbar_try_wait(bar, parity)) return true;
-    const unsigned long long start = global_ns();
-    for (;;) {
-        if (mbar_try_wait(bar, parity)) return true;
-        if (global_ns() - start > kWaitLimitNs) return false;
-    }
-}
-
-__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-            smem_addr(dst)),
-        "l"(src), "r"(bytes), "r"(smem_addr(bar))
-        : "memory");
-}
 
 // Stage layout: slot k (plane k for k < 7, the solid plane for k = 7) holds
 // R rows of Pq words; staged row r of every slot feeds output row y0 + r, so

@@ -27,9 +27,10 @@ def fhp_mod():
     return pkg
 
 
-def gpu_run(pkg, s0, seed, t0, n, p, chunks=None, kernel=0):
+def gpu_run(pkg, s0, seed, t0, n, p, chunks=None, kernel=0, k_block=1):
     H, W = s0.shape
     with pkg.Lattice(W, H, seed=seed, forcing_p=p, step_kernel=kernel) as lat:
+        lat.set_temporal_block(k_block)
         lat.set_state(s0)
         lat.set_time(t0)
         for c in (chunks or [n]):
@@ -109,6 +110,54 @@ def test_parity_ring_many_tiles(fhp_mod, oracle_mod, W, H, kernel):
     want, _ = oracle_mod.run(s0, seed, 0, 7, 0.01)
     got = gpu_run(fhp_mod, s0, seed, 0, 7, 0.01, kernel=kernel)
     assert_same(got, want, f"kernel {kernel} {W}x{H}")
+
+
+@pytest.mark.parametrize("k", [2, 4, 8])
+@pytest.mark.parametrize("W,H", [(512, 18), (640, 46), (4224, 100), (2048, 512), (4096, 1030)])
+@pytest.mark.parametrize("variant", ["periodic", "walls_forcing", "points_forcing"])
+def test_parity_temporal_block(fhp_mod, oracle_mod, W, H, k, variant):
+    """k steps per pass in shared memory (2-D tiles with a k-row / 128-node
+    halo, periodic wrap of the halo in x and y): bit-exact for passes plus a
+    remainder of single steps."""
+    seed = 77 + W + H + k
+    rng = np.random.Generator(np.random.PCG64(seed))
+    if variant == "periodic":
+        solid, p = None, 0.0
+    elif variant == "walls_forcing":
+        solid, p = workloads.channel_walls(W, H), 0.05
+    else:
+        solid, p = workloads.random_points(W, H, 0.05, rng), 0.2
+    s0 = workloads.bernoulli_lattice(W, H, 0.35, seed, solid)
+    steps = 2 * k + 3
+    want, _ = oracle_mod.run(s0, seed, 5, steps, p)
+    got = gpu_run(fhp_mod, s0, seed, 5, steps, p, k_block=k)
+    assert_same(got, want, f"{W}x{H} {variant} k={k}")
+
+
+@pytest.mark.parametrize("k", [4, 8])
+def test_temporal_block_forcing_near_tile_edges(fhp_mod, oracle_mod, k):
+    """Forcing decides the 32 nodes of a word together, so an inexact node at
+    the edge of a staged block spoils its whole word: the horizontal halo must
+    be k words.  Dense forcing on the smallest supported height and several
+    seeds exercises exactly that."""
+    W, H = 512, 2 * k + 2
+    for seed in range(600, 608):
+        rng = np.random.Generator(np.random.PCG64(seed))
+        s0 = workloads.bernoulli_lattice(W, H, 0.35, seed, workloads.random_points(W, H, 0.05, rng))
+        for p in (0.2, 0.5):
+            want, _ = oracle_mod.run(s0, seed, 5, k, p)
+            got = gpu_run(fhp_mod, s0, seed, 5, k, p, k_block=k)
+            assert_same(got, want, f"seed {seed} p {p} k {k}")
+
+
+def test_temporal_block_full_size_all_k(fhp_mod, oracle_mod):
+    """16384 x 4096 cylinder: 24 steps give the same state for k = 1, 2, 4, 8
+    and equal the oracle."""
+    job = workloads.cylinder_16384x4096()
+    s0 = job.initial_state()
+    want, _ = oracle_mod.run(s0, job.seed, 0, 24, job.p)
+    for k in (1, 2, 4, 8):
+        assert_same(gpu_run(fhp_mod, s0, job.seed, 0, 24, job.p, k_block=k), want, f"k={k}")
 
 
 def test_parity_large_step_counter(fhp_mod, oracle_mod):
