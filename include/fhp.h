@@ -182,6 +182,71 @@ FHP_API int64_t fhp_kernel_launches(const fhp_lattice* lattice);
 FHP_API int fhp_philox4x32_10_device(const uint32_t* device_ctr, const uint32_t* device_key,
                              uint32_t* device_out, int64_t n, void* stream);
 
+/* ------------------------------------------------------------------------
+ * Batches: many independent lattices advanced by shared kernel launches.
+ *
+ * A batch owns one device arena (library- or caller-allocated).  Members --
+ * lattices of any size (W a multiple of 32 up to 32,768, H even), each with
+ * its own seed, forcing probability, obstacles, step counter and optional
+ * step budget -- are carved out of the arena and may be added or removed
+ * between calls, while the others keep their state.  fhp_batch_step(n)
+ * advances every member by min(n, its remaining budget) steps; each step is
+ * one kernel launch over the tiles of all members (replayed from a captured
+ * CUDA graph), and every member evolves exactly as it would alone.
+ * Slots are small integers, reused after fhp_batch_remove.  Calls on one
+ * batch must not overlap in time.  Errors: FHP_EINVAL for bad slots or
+ * arguments, FHP_ENOMEM when the arena cannot hold a new member (admission
+ * control), FHP_ECUDA for CUDA failures; fhp_batch_last_error explains.
+ * ------------------------------------------------------------------------ */
+typedef struct fhp_batch fhp_batch;
+
+/* Arena bytes one member of W x H nodes occupies (0 if it cannot be a
+ * member).  Set/get state and coarse-graining briefly need W*H (resp. the
+ * coarse fields) more, also taken from the arena. */
+FHP_API size_t fhp_batch_lattice_bytes(int32_t width, int32_t height);
+
+/* Create an empty batch with an arena of arena_bytes on the current device:
+ * caller-owned if device_memory is not NULL (256-byte aligned, kept alive by
+ * the caller until fhp_batch_destroy), else allocated by the library.  Work
+ * is enqueued on `stream` (cudaStream_t, NULL = legacy default stream). */
+FHP_API int fhp_batch_create(fhp_batch** out, size_t arena_bytes, void* device_memory, void* stream);
+FHP_API void fhp_batch_destroy(fhp_batch* batch);
+FHP_API const char* fhp_batch_last_error(const fhp_batch* batch);
+
+/* Add an empty, all-fluid member at step 0 without a step budget; *slot
+ * receives its slot.  FHP_ENOMEM if the arena has no room. */
+FHP_API int fhp_batch_add(fhp_batch* batch, int32_t width, int32_t height, uint64_t seed, double forcing_p,
+                          int32_t* slot);
+/* Remove a member and return its memory to the arena (waits for queued work). */
+FHP_API int fhp_batch_remove(fhp_batch* batch, int32_t slot);
+
+/* Member state as H x W node bytes (as fhp_set_state / fhp_get_state). */
+FHP_API int fhp_batch_set_state(fhp_batch* batch, int32_t slot, const uint8_t* host_bytes);
+FHP_API int fhp_batch_get_state(fhp_batch* batch, int32_t slot, uint8_t* host_bytes);
+FHP_API int fhp_batch_set_time(fhp_batch* batch, int32_t slot, int64_t t);
+FHP_API int64_t fhp_batch_get_time(const fhp_batch* batch, int32_t slot);
+
+/* Step budget of a member: fhp_batch_step advances it by at most this many
+ * more steps (-1 = no budget, the default). */
+FHP_API int fhp_batch_set_steps_left(fhp_batch* batch, int32_t slot, int64_t steps);
+FHP_API int64_t fhp_batch_get_steps_left(const fhp_batch* batch, int32_t slot);
+
+/* Advance every member by min(n, its budget) steps.  Asynchronous. */
+FHP_API int fhp_batch_step(fhp_batch* batch, int64_t n);
+
+/* Steps per captured CUDA graph of batch launches (0: launch directly). */
+FHP_API int fhp_batch_set_graph_steps(fhp_batch* batch, int32_t steps);
+
+/* Coarse-grain one member into host buffers (as fhp_coarse_grain). */
+FHP_API int fhp_batch_coarse_grain(fhp_batch* batch, int32_t slot, int32_t block, int32_t* host_counts,
+                                   float* host_rho, float* host_ux, float* host_uy);
+
+/* Wait for queued work; FHP_ETIMEOUT if a batch kernel gave up waiting. */
+FHP_API int fhp_batch_synchronize(fhp_batch* batch);
+FHP_API int32_t fhp_batch_count(const fhp_batch* batch);
+FHP_API size_t fhp_batch_free_bytes(const fhp_batch* batch);
+FHP_API int64_t fhp_batch_kernel_launches(const fhp_batch* batch);
+
 /* Size in bytes of the device array that fhp_run_static works in. */
 #define FHP_STATIC_SCRATCH_BYTES (16u << 20)
 

@@ -4,6 +4,6 @@ The update runs in hand-written CUDA for sm_103a behind the C ABI of
 ``include/fhp.h``; this package holds the CUDA sources (``csrc/``), their
 build (``build.py``) and the ctypes binding (``fhp.py``).
 """
-from .fhp import FhpError, Lattice, load, philox4x32_10_device, required_bytes  # noqa: F401
+from .fhp import Batch, FhpError, Lattice, load, philox4x32_10_device, required_bytes  # noqa: F401
 
-__all__ = ["FhpError", "Lattice", "load", "philox4x32_10_device", "required_bytes"]
+__all__ = ["Batch", "FhpError", "Lattice", "load", "philox4x32_10_device", "required_bytes"]

@@ -1,0 +1,744 @@
+// fhp_batch.cu -- many independent FHP lattices advanced by shared launches.
+//
+// A batch owns one device arena.  Member lattices (any sizes, seeds, forcing
+// probabilities, obstacle maps) are carved out of it and may join or leave
+// between calls.  fhp_batch_step(n) advances every member by
+// min(n, its step budget) steps; each step is ONE launch of fhp_batch_kernel
+// over a tile list that spans all members, and the per-step launches are
+// replayed from a captured CUDA graph.
+//
+// fhp_batch_kernel is the warp-specialised ring of the single-lattice path
+// (producer warp streaming row tiles into a 3-stage shared-memory ring with
+// cp.async.bulk, 8 consumer warps computing), except that every tile may
+// belong to a different lattice: the producer copies that lattice's
+// descriptor (geometry, buffers, generator key, step, forcing table) into a
+// per-stage header in shared memory, and the consumers run the same per-quad
+// code against it.  Members whose budget is used up are skipped.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/fhp.h"
+#include "fhp_arena.h"
+#include "fhp_device.cuh"
+#include "fhp_internal.h"
+#include "fhp_quad.cuh"
+
+namespace fhp {
+namespace {
+
+constexpr int kBConsumerWarps = 8;
+constexpr int kBThreads = (kBConsumerWarps + 1) * 32;
+constexpr int kBStages = 3;
+constexpr int kBStageBudget = 32 * 1024;
+
+// Device descriptor of one member lattice.
+struct BatchLattice {
+    StepArgs a;               // geometry, solid plane, key, forcing table, err
+    TileArgs ta;              // rows per tile (ntiles unused)
+    uint32_t* buf[2];
+    unsigned long long t0;    // step counter at the start of the current call
+    int cur;                  // buffer holding S_{t0}
+    int steps;                // steps in the current call (0: idle)
+    int force;
+    int pad;
+};
+
+struct BatchTile {
+    int lattice;
+    int tile;                 // row tile index within the lattice
+};
+
+// Written by the producer warp for every staged tile.
+struct __align__(16) StageHeader {
+    StepArgs a;               // with src/dst/t of this step
+    TileArgs ta;
+    int tile;
+    int active;
+    int force;
+    int pad;
+};
+
+constexpr int kHeaderBytes = (int)((sizeof(StageHeader) + 127) / 128 * 128);
+constexpr int kBPrefixBytes = 128 + kBStages * kHeaderBytes;  // barriers, then headers
+
+template <bool FORCE>
+__device__ __forceinline__ void batch_compute(const StageHeader& h, const uint32_t* stage) {
+    const StepVar v{h.a.dst, h.a.t_lo, h.a.t_hi};
+    compute_tile<true, FORCE, true>(h.a, v, h.ta, h.tile, stage, (int)threadIdx.x, kBConsumerWarps * 32);
+}
+
+__global__ void __launch_bounds__(kBThreads, 2)
+    fhp_batch_kernel(const BatchLattice* __restrict__ lats, const BatchTile* __restrict__ tiles, int ntiles,
+                     const int* __restrict__ step_base, int step_offset, unsigned int* err) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw);
+    uint64_t* empty = full + kBStages;
+    StageHeader* headers = reinterpret_cast<StageHeader*>(smem_raw + 128);
+    uint32_t* stages = reinterpret_cast<uint32_t*>(smem_raw + kBPrefixBytes);
+    const int stage_words = kBStageBudget / 4;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int count = (ntiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
+    const int s = *step_base + step_offset;  // step index within the current call
+
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < kBStages; ++k) {
+            mbar_init(&full[k], 1);
+            mbar_init(&empty[k], kBConsumerWarps);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+
+    if (warp == kBConsumerWarps) {
+        bool ok = true;
+        int i = 0;
+        for (; i < count; ++i) {
+            const int st = i % kBStages;
+            int waited = 1;
+            if (lane == 0 && i >= kBStages)
+                waited = mbar_wait_bounded(&empty[st], (uint32_t)(((i / kBStages) - 1) & 1)) ? 1 : 0;
+            if (!__shfl_sync(0xFFFFFFFFu, waited, 0)) {
+                ok = false;
+                break;
+            }
+            __syncwarp();  // order lane 0's acquire of "empty" before the lanes rewrite the header
+            const BatchTile bt = tiles[blockIdx.x + i * gridDim.x];
+            const BatchLattice* L = lats + bt.lattice;
+            StageHeader* h = headers + st;
+            // The lanes copy the lattice's StepArgs into the header.
+            {
+                const uint32_t* srcw = reinterpret_cast<const uint32_t*>(&L->a);
+                uint32_t* dstw = reinterpret_cast<uint32_t*>(&h->a);
+                for (int w = lane; w < (int)(sizeof(StepArgs) / 4); w += 32) dstw[w] = srcw[w];
+            }
+            __syncwarp();
+            if (lane == 0) {
+                const int active = s < L->steps;
+                const int par = (L->cur + s) & 1;
+                const unsigned long long t = L->t0 + (unsigned long long)s;
+                h->a.src = L->buf[par];
+                h->a.dst = L->buf[par ^ 1];
+                h->a.t_lo = (uint32_t)t;
+                h->a.t_hi = (uint32_t)(t >> 32);
+                h->a.err = err;
+                h->ta = L->ta;
+                h->tile = bt.tile;
+                h->active = active;
+                h->force = L->force;
+                if (active) {
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    issue_tile<true>(h->a, h->ta, h->a.src, bt.tile, stages + (size_t)st * stage_words, &full[st]);
+                } else {
+                    mbar_arrive_expect_tx(&full[st], 0u);  // nothing to stage: release the stage at once
+                }
+            }
+            __syncwarp();
+        }
+        if (lane == 0) {
+            if (!ok && err) atomicOr(err, 1u);
+            for (int k = (i > kBStages ? i - kBStages : 0); k < i; ++k)
+                (void)mbar_wait_bounded(&full[k % kBStages], (uint32_t)((k / kBStages) & 1));
+        }
+        return;
+    }
+
+    for (int i = 0; i < count; ++i) {
+        const int st = i % kBStages;
+        if (!mbar_wait_bounded(&full[st], (uint32_t)((i / kBStages) & 1))) {
+            if (lane == 0 && err) atomicOr(err, 1u);
+            return;
+        }
+        const StageHeader& h = headers[st];
+        if (h.active) {
+            if (h.force) batch_compute<true>(h, stages + (size_t)st * stage_words);
+            else batch_compute<false>(h, stages + (size_t)st * stage_words);
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[st]);
+    }
+}
+
+__global__ void advance_kernel(int* step_base, int by) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) *step_base += by;
+}
+
+int batch_blocks_per_sm(int dev, cudaError_t* e) {
+    static std::mutex m;
+    static int cached[64] = {};
+    std::lock_guard<std::mutex> lock(m);
+    if (dev < 0 || dev >= 64) {
+        *e = cudaErrorInvalidDevice;
+        return 0;
+    }
+    if (!cached[dev]) {
+        const int smem = kBPrefixBytes + kBStages * kBStageBudget;
+        *e = cudaFuncSetAttribute(fhp_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (*e != cudaSuccess) return 0;
+        int n = 0;
+        *e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fhp_batch_kernel, kBThreads, smem);
+        if (*e != cudaSuccess) return 0;
+        cached[dev] = n > 0 ? n : 1;
+    }
+    *e = cudaSuccess;
+    return cached[dev];
+}
+
+size_t round256(size_t v) { return (v + 255) / 256 * 256; }
+
+}  // namespace
+}  // namespace fhp
+
+// ---------------------------------------------------------------------------
+// Host side: the batch object.
+// ---------------------------------------------------------------------------
+namespace {
+
+struct Member {
+    bool used = false;
+    fhp::Geometry g;
+    uint64_t seed = 0;
+    double p = 0.0;
+    fhp::ForcingTable ft{};
+    size_t off = 0, bytes = 0;    // arena block
+    uint32_t* buf[2] = {nullptr, nullptr};
+    uint32_t* solid = nullptr;
+    unsigned int* flags = nullptr;
+    int cur = 0;
+    int64_t t = 0;
+    int64_t steps_left = -1;      // -1: no budget
+    bool has_solid = false;
+    int R = 1;
+};
+
+constexpr int64_t kMaxTime = (int64_t)1 << 48;
+
+size_t member_bytes(const fhp::Geometry& g) {
+    return 15 * fhp::round256(g.plane_words * sizeof(uint32_t)) + 256;
+}
+
+fhp::ForcingTable forcing_thresholds(double p) {
+    const unsigned long long one = 1ULL << 32;
+    unsigned long long P;
+    const double scaled = std::ldexp(p, 32);
+    if (!(scaled > 0.0)) P = 0;
+    else if (scaled >= std::ldexp(1.0, 32)) P = one;
+    else P = (unsigned long long)std::nearbyint(scaled);
+    fhp::ForcingTable ft;
+    unsigned long long S = one;
+    ft.p_plus_1 = P + 1;
+    ft.q[0] = 0;
+    for (int g = 1; g <= 32; ++g) {
+        S = (unsigned long long)(((unsigned __int128)S * (one - P)) >> 32);
+        ft.q[g] = one - S;
+    }
+    return ft;
+}
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+        else prev = -1;
+    }
+    ~DeviceGuard() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+}  // namespace
+
+struct fhp_batch {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    uint8_t* arena_base = nullptr;
+    bool owns_arena = false;
+    fhp::Arena arena;
+    std::vector<Member> members;
+    // device tables (allocated from the arena, grown on demand)
+    size_t lat_off = SIZE_MAX, lat_cap = 0;     // BatchLattice entries
+    size_t tile_off = SIZE_MAX, tile_cap = 0;   // BatchTile entries
+    size_t misc_off = SIZE_MAX;                 // step base + error word
+    fhp::BatchLattice* d_lats = nullptr;
+    fhp::BatchTile* d_tiles = nullptr;
+    int* d_step_base = nullptr;
+    unsigned int* d_err = nullptr;
+    std::vector<fhp::BatchLattice> h_lats;
+    std::vector<fhp::BatchTile> h_tiles;
+    bool tiles_dirty = true;
+    int ntiles = 0;
+    int graph_steps = 64;
+    cudaGraphExec_t graph = nullptr;
+    int graph_ntiles = -1;
+    int64_t launches = 0;
+    std::string err;
+};
+
+namespace {
+
+int bfail(fhp_batch* b, int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (b) b->err = buf;
+    else fhp::set_thread_error(buf);
+    return code;
+}
+
+int bcuda(fhp_batch* b, cudaError_t e, const char* what) {
+    return bfail(b, FHP_ECUDA, "%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
+}
+
+Member* member(fhp_batch* b, int32_t slot) {
+    if (!b || slot < 0 || slot >= (int32_t)b->members.size() || !b->members[slot].used) return nullptr;
+    return &b->members[slot];
+}
+
+void drop_graph(fhp_batch* b) {
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+    b->graph_ntiles = -1;
+}
+
+// Make sure the device tables can hold `lats` lattices and `tiles` tiles.
+int ensure_tables(fhp_batch* b, size_t lats, size_t tiles) {
+    if (lats > b->lat_cap) {
+        const size_t cap = std::max<size_t>(lats, 2 * b->lat_cap + 16);
+        const size_t off = b->arena.allocate(cap * sizeof(fhp::BatchLattice));
+        if (off == SIZE_MAX) return bfail(b, FHP_ENOMEM, "batch arena full (descriptor table)");
+        if (b->lat_off != SIZE_MAX) b->arena.release(b->lat_off, b->lat_cap * sizeof(fhp::BatchLattice));
+        b->lat_off = off;
+        b->lat_cap = cap;
+        b->d_lats = (fhp::BatchLattice*)(b->arena_base + off);
+        drop_graph(b);
+    }
+    if (tiles > b->tile_cap) {
+        const size_t cap = std::max<size_t>(tiles, 2 * b->tile_cap + 256);
+        const size_t off = b->arena.allocate(cap * sizeof(fhp::BatchTile));
+        if (off == SIZE_MAX) return bfail(b, FHP_ENOMEM, "batch arena full (tile table)");
+        if (b->tile_off != SIZE_MAX) b->arena.release(b->tile_off, b->tile_cap * sizeof(fhp::BatchTile));
+        b->tile_off = off;
+        b->tile_cap = cap;
+        b->d_tiles = (fhp::BatchTile*)(b->arena_base + off);
+        drop_graph(b);
+    }
+    return FHP_OK;
+}
+
+// Rows per tile: about 256 quads per tile (one per consumer thread), and
+// the tile's 8 planes within one stage.
+int rows_per_tile(const fhp::Geometry& g) {
+    const long long row_bytes = 8LL * g.Pq * 4;
+    int R = (256 + g.nq - 1) / g.nq;
+    const int fit = (int)(fhp::kBStageBudget / row_bytes);
+    R = std::min(R, fit);
+    R = std::min(R, g.H);
+    return R < 1 ? 1 : R;
+}
+
+int scratch_bytes_op(fhp_batch* b, size_t bytes, size_t* off) {
+    *off = b->arena.allocate(bytes);
+    if (*off == SIZE_MAX) return bfail(b, FHP_ENOMEM, "batch arena full (staging of %zu bytes)", bytes);
+    return FHP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t fhp_batch_lattice_bytes(int32_t width, int32_t height) {
+    if (width < 32 || width % 32 || height < 2 || height % 2) return 0;
+    const fhp::Geometry g = fhp::make_geometry(width, height);
+    if (8LL * g.Pq * 4 > fhp::kBStageBudget) return 0;
+    return member_bytes(g);
+}
+
+int fhp_batch_create(fhp_batch** out, size_t arena_bytes, void* device_memory, void* stream) {
+    if (!out) return bfail(nullptr, FHP_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (arena_bytes < 65536) return bfail(nullptr, FHP_EINVAL, "arena of %zu bytes is too small", arena_bytes);
+    fhp_batch* b = new (std::nothrow) fhp_batch();
+    if (!b) return bfail(nullptr, FHP_ENOMEM, "host allocation failed");
+    cudaError_t e = cudaGetDevice(&b->device);
+    if (e != cudaSuccess) {
+        delete b;
+        return bfail(nullptr, FHP_ECUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
+    }
+    b->stream = (cudaStream_t)stream;
+    if (device_memory) {
+        if ((uintptr_t)device_memory & 255u) {
+            delete b;
+            return bfail(nullptr, FHP_EINVAL, "device_memory must be 256-byte aligned");
+        }
+        b->arena_base = (uint8_t*)device_memory;
+        b->owns_arena = false;
+    } else {
+        e = cudaMalloc((void**)&b->arena_base, arena_bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            delete b;
+            return bfail(nullptr, FHP_ENOMEM, "cudaMalloc(%zu): %s", arena_bytes, cudaGetErrorString(e));
+        }
+        b->owns_arena = true;
+    }
+    b->arena.reset(arena_bytes);
+    b->misc_off = b->arena.allocate(256);
+    b->d_step_base = (int*)(b->arena_base + b->misc_off);
+    b->d_err = (unsigned int*)(b->arena_base + b->misc_off + 64);
+    e = cudaMemsetAsync(b->arena_base + b->misc_off, 0, 256, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) {
+        if (b->owns_arena) cudaFree(b->arena_base);
+        delete b;
+        return bfail(nullptr, FHP_ECUDA, "initialising the batch: %s", cudaGetErrorString(e));
+    }
+    *out = b;
+    return FHP_OK;
+}
+
+void fhp_batch_destroy(fhp_batch* b) {
+    if (!b) return;
+    DeviceGuard dg(b->device);
+    cudaStreamSynchronize(b->stream);
+    drop_graph(b);
+    if (b->owns_arena && b->arena_base) cudaFree(b->arena_base);
+    delete b;
+}
+
+const char* fhp_batch_last_error(const fhp_batch* b) { return b ? b->err.c_str() : ""; }
+
+int fhp_batch_add(fhp_batch* b, int32_t width, int32_t height, uint64_t seed, double forcing_p,
+                  int32_t* out_slot) {
+    if (!b || !out_slot) return bfail(b, FHP_EINVAL, "NULL argument");
+    *out_slot = -1;
+    if (width < 32 || width % 32 || height < 2 || height % 2)
+        return bfail(b, FHP_EINVAL, "invalid lattice %d x %d", width, height);
+    if (!(forcing_p >= 0.0 && forcing_p <= 1.0)) return bfail(b, FHP_EINVAL, "forcing probability outside [0, 1]");
+    const fhp::Geometry g = fhp::make_geometry(width, height);
+    if (8LL * g.Pq * 4 > fhp::kBStageBudget)
+        return bfail(b, FHP_EINVAL, "rows of %d nodes are too wide for a batch member", width);
+    DeviceGuard dg(b->device);
+    Member m;
+    m.used = true;
+    m.g = g;
+    m.seed = seed;
+    m.p = forcing_p;
+    m.ft = forcing_thresholds(forcing_p);
+    m.bytes = member_bytes(g);
+    m.off = b->arena.allocate(m.bytes);
+    if (m.off == SIZE_MAX) return bfail(b, FHP_ENOMEM, "batch arena full: a %d x %d lattice needs %zu bytes", width, height, m.bytes);
+    const size_t pb = fhp::round256(g.plane_words * sizeof(uint32_t));
+    uint8_t* base = b->arena_base + m.off;
+    m.buf[0] = (uint32_t*)base;
+    m.buf[1] = (uint32_t*)(base + 7 * pb);
+    m.solid = (uint32_t*)(base + 14 * pb);
+    m.flags = (unsigned int*)(base + 15 * pb);
+    m.R = rows_per_tile(g);
+    cudaError_t e = cudaMemsetAsync(base, 0, m.bytes, b->stream);
+    if (e != cudaSuccess) {
+        b->arena.release(m.off, m.bytes);
+        return bcuda(b, e, "clearing a new member");
+    }
+    int32_t slot = -1;
+    for (size_t i = 0; i < b->members.size(); ++i)
+        if (!b->members[i].used) { slot = (int32_t)i; break; }
+    if (slot < 0) {
+        slot = (int32_t)b->members.size();
+        b->members.push_back(m);
+    } else {
+        b->members[slot] = m;
+    }
+    b->tiles_dirty = true;
+    *out_slot = slot;
+    return FHP_OK;
+}
+
+int fhp_batch_remove(fhp_batch* b, int32_t slot) {
+    Member* m = member(b, slot);
+    if (!m) return bfail(b, FHP_EINVAL, "no member in slot %d", slot);
+    DeviceGuard dg(b->device);
+    cudaError_t e = cudaStreamSynchronize(b->stream);  // nothing may still use its memory
+    if (e != cudaSuccess) return bcuda(b, e, "synchronizing");
+    b->arena.release(m->off, m->bytes);
+    *m = Member();
+    b->tiles_dirty = true;
+    return FHP_OK;
+}
+
+int fhp_batch_set_state(fhp_batch* b, int32_t slot, const uint8_t* host_bytes) {
+    Member* m = member(b, slot);
+    if (!m || !host_bytes) return bfail(b, FHP_EINVAL, "invalid slot %d or NULL bytes", slot);
+    DeviceGuard dg(b->device);
+    const size_t n = (size_t)m->g.W * m->g.H;
+    size_t off;
+    int rc = scratch_bytes_op(b, n, &off);
+    if (rc != FHP_OK) return rc;
+    uint8_t* staging = b->arena_base + off;
+    cudaError_t e = cudaMemcpyAsync(staging, host_bytes, n, cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(m->flags, 0, sizeof(unsigned int), b->stream);
+    if (e == cudaSuccess) e = fhp::launch_pack(m->g, staging, m->buf[m->cur], m->solid, m->flags, b->stream);
+    unsigned int flag = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&flag, m->flags, sizeof flag, cudaMemcpyDeviceToHost, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    b->arena.release(off, n);
+    if (e != cudaSuccess) return bcuda(b, e, "setting a member's state");
+    ++b->launches;
+    m->has_solid = flag != 0;
+    return FHP_OK;
+}
+
+int fhp_batch_get_state(fhp_batch* b, int32_t slot, uint8_t* host_bytes) {
+    Member* m = member(b, slot);
+    if (!m || !host_bytes) return bfail(b, FHP_EINVAL, "invalid slot %d or NULL bytes", slot);
+    DeviceGuard dg(b->device);
+    const size_t n = (size_t)m->g.W * m->g.H;
+    size_t off;
+    int rc = scratch_bytes_op(b, n, &off);
+    if (rc != FHP_OK) return rc;
+    uint8_t* staging = b->arena_base + off;
+    cudaError_t e = fhp::launch_unpack(m->g, m->buf[m->cur], m->solid, staging, b->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(host_bytes, staging, n, cudaMemcpyDeviceToHost, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    b->arena.release(off, n);
+    if (e != cudaSuccess) return bcuda(b, e, "reading a member's state");
+    ++b->launches;
+    return FHP_OK;
+}
+
+int fhp_batch_coarse_grain(fhp_batch* b, int32_t slot, int32_t block, int32_t* counts, float* rho, float* ux,
+                           float* uy) {
+    Member* m = member(b, slot);
+    if (!m) return bfail(b, FHP_EINVAL, "no member in slot %d", slot);
+    if (block < 32 || block % 32 || m->g.W % block || m->g.H % block)
+        return bfail(b, FHP_EINVAL, "coarse-grain block %d must be a multiple of 32 dividing %d and %d", block,
+                     m->g.W, m->g.H);
+    DeviceGuard dg(b->device);
+    const size_t cells = (size_t)(m->g.W / block) * (m->g.H / block);
+    const size_t bc = fhp::round256(cells * 9 * sizeof(int32_t)), bf = fhp::round256(cells * sizeof(float));
+    size_t off;
+    int rc = scratch_bytes_op(b, bc + 3 * bf, &off);
+    if (rc != FHP_OK) return rc;
+    uint8_t* s = b->arena_base + off;
+    int32_t* dc = (int32_t*)s;
+    float* dr = (float*)(s + bc);
+    float* dx = (float*)(s + bc + bf);
+    float* dy = (float*)(s + bc + 2 * bf);
+    cudaError_t e = fhp::launch_coarse_grain(m->g, m->buf[m->cur], m->solid, m->has_solid, block, dc, dr, dx, dy,
+                                             b->stream);
+    if (e == cudaSuccess && counts) e = cudaMemcpyAsync(counts, dc, cells * 9 * 4, cudaMemcpyDeviceToHost, b->stream);
+    if (e == cudaSuccess && rho) e = cudaMemcpyAsync(rho, dr, cells * 4, cudaMemcpyDeviceToHost, b->stream);
+    if (e == cudaSuccess && ux) e = cudaMemcpyAsync(ux, dx, cells * 4, cudaMemcpyDeviceToHost, b->stream);
+    if (e == cudaSuccess && uy) e = cudaMemcpyAsync(uy, dy, cells * 4, cudaMemcpyDeviceToHost, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    b->arena.release(off, bc + 3 * bf);
+    if (e != cudaSuccess) return bcuda(b, e, "coarse-graining a member");
+    ++b->launches;
+    return FHP_OK;
+}
+
+int fhp_batch_set_time(fhp_batch* b, int32_t slot, int64_t t) {
+    Member* m = member(b, slot);
+    if (!m || t < 0 || t >= kMaxTime) return bfail(b, FHP_EINVAL, "invalid slot or time");
+    m->t = t;
+    return FHP_OK;
+}
+
+int64_t fhp_batch_get_time(const fhp_batch* b, int32_t slot) {
+    Member* m = member(const_cast<fhp_batch*>(b), slot);
+    return m ? m->t : -1;
+}
+
+int fhp_batch_set_steps_left(fhp_batch* b, int32_t slot, int64_t n) {
+    Member* m = member(b, slot);
+    if (!m || n < -1) return bfail(b, FHP_EINVAL, "invalid slot or step budget");
+    m->steps_left = n;
+    return FHP_OK;
+}
+
+int64_t fhp_batch_get_steps_left(const fhp_batch* b, int32_t slot) {
+    Member* m = member(const_cast<fhp_batch*>(b), slot);
+    return m ? m->steps_left : -2;
+}
+
+int fhp_batch_set_graph_steps(fhp_batch* b, int32_t steps) {
+    if (!b || steps < 0) return bfail(b, FHP_EINVAL, "invalid graph step count");
+    b->graph_steps = steps;
+    drop_graph(b);
+    return FHP_OK;
+}
+
+int fhp_batch_step(fhp_batch* b, int64_t n) {
+    if (!b || n < 0) return bfail(b, FHP_EINVAL, "invalid arguments");
+    DeviceGuard dg(b->device);
+    // Per-member step counts for this call.
+    int max_steps = 0;
+    const int64_t cap = n < (1 << 30) ? n : (1 << 30);
+    for (auto& m : b->members) {
+        if (!m.used) continue;
+        int64_t k = cap;
+        if (m.steps_left >= 0 && m.steps_left < k) k = m.steps_left;
+        if (m.t + k >= kMaxTime) return bfail(b, FHP_EINVAL, "a member's step counter would pass 2^48");
+        max_steps = std::max<int>(max_steps, (int)k);
+    }
+    if (max_steps == 0) return FHP_OK;
+    // Descriptors and tile list.
+    const size_t nm = b->members.size();
+    int rc = FHP_OK;
+    if (b->tiles_dirty) {
+        b->h_tiles.clear();
+        for (size_t i = 0; i < nm; ++i) {
+            const Member& m = b->members[i];
+            if (!m.used) continue;
+            const int nt = (m.g.H + m.R - 1) / m.R;
+            for (int j = 0; j < nt; ++j) b->h_tiles.push_back(fhp::BatchTile{(int)i, j});
+        }
+        rc = ensure_tables(b, std::max<size_t>(nm, 1), std::max<size_t>(b->h_tiles.size(), 1));
+        if (rc != FHP_OK) return rc;
+        cudaError_t e = cudaMemcpyAsync(b->d_tiles, b->h_tiles.data(), b->h_tiles.size() * sizeof(fhp::BatchTile),
+                                        cudaMemcpyHostToDevice, b->stream);
+        if (e != cudaSuccess) return bcuda(b, e, "uploading the tile list");
+        b->ntiles = (int)b->h_tiles.size();
+        b->tiles_dirty = false;
+        drop_graph(b);
+    }
+    rc = ensure_tables(b, std::max<size_t>(nm, 1), std::max<size_t>(b->h_tiles.size(), 1));
+    if (rc != FHP_OK) return rc;
+    b->h_lats.assign(nm, fhp::BatchLattice{});
+    std::vector<int> steps_of(nm, 0);
+    for (size_t i = 0; i < nm; ++i) {
+        const Member& m = b->members[i];
+        fhp::BatchLattice& L = b->h_lats[i];
+        if (!m.used) continue;
+        int64_t k = cap;
+        if (m.steps_left >= 0 && m.steps_left < k) k = m.steps_left;
+        steps_of[i] = (int)k;
+        L.a.src = m.buf[m.cur];
+        L.a.dst = m.buf[m.cur ^ 1];
+        L.a.solid = m.solid;
+        L.a.plane_words = m.g.plane_words;
+        L.a.H = m.g.H;
+        L.a.Wq = m.g.Wq;
+        L.a.nq = m.g.nq;
+        L.a.Pq = m.g.Pq;
+        L.a.rows_per_warp = L.a.groups_per_parity = L.a.warps_per_row = 1;
+        L.a.key = fhp::Key2{(uint32_t)m.seed, (uint32_t)(m.seed >> 32)};
+        L.a.t_lo = (uint32_t)m.t;
+        L.a.t_hi = (uint32_t)(m.t >> 32);
+        L.a.err = b->d_err;
+        L.a.ft = m.ft;
+        L.ta.R = m.R;
+        L.ta.ntiles = (m.g.H + m.R - 1) / m.R;
+        L.ta.nq_magic = ((1ull << 32) + m.g.nq - 1) / m.g.nq;
+        L.buf[0] = m.buf[0];
+        L.buf[1] = m.buf[1];
+        L.t0 = (unsigned long long)m.t;
+        L.cur = m.cur;
+        L.steps = (int)k;
+        L.force = m.ft.q[32] != 0;
+    }
+    cudaError_t e = cudaMemcpyAsync(b->d_lats, b->h_lats.data(), nm * sizeof(fhp::BatchLattice),
+                                    cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_step_base, 0, sizeof(int), b->stream);
+    if (e != cudaSuccess) return bcuda(b, e, "uploading the descriptors");
+    int bps = fhp::batch_blocks_per_sm(b->device, &e);
+    if (e != cudaSuccess) return bcuda(b, e, "configuring the batch kernel");
+    int sms = 0;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
+    if (e != cudaSuccess) return bcuda(b, e, "querying the SM count");
+    const int grid = std::min(b->ntiles, bps * sms);
+    const size_t smem = fhp::kBPrefixBytes + fhp::kBStages * fhp::kBStageBudget;
+    auto launch_steps = [&](int first, int count) -> cudaError_t {
+        for (int o = first; o < first + count; ++o) {
+            fhp::fhp_batch_kernel<<<grid, fhp::kBThreads, smem, b->stream>>>(b->d_lats, b->d_tiles, b->ntiles,
+                                                                              b->d_step_base, o, b->d_err);
+            cudaError_t le = cudaGetLastError();
+            if (le != cudaSuccess) return le;
+        }
+        return cudaSuccess;
+    };
+    int done = 0;
+    const int G = b->graph_steps;
+    if (G > 0 && max_steps >= G) {
+        if (!b->graph || b->graph_ntiles != b->ntiles) {
+            drop_graph(b);
+            cudaStream_t cs;
+            e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+            if (e != cudaSuccess) return bcuda(b, e, "creating the capture stream");
+            cudaGraph_t graph = nullptr;
+            e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+            if (e == cudaSuccess) {
+                for (int o = 0; o < G; ++o)
+                    fhp::fhp_batch_kernel<<<grid, fhp::kBThreads, smem, cs>>>(b->d_lats, b->d_tiles, b->ntiles,
+                                                                               b->d_step_base, o, b->d_err);
+                fhp::advance_kernel<<<1, 32, 0, cs>>>(b->d_step_base, G);
+                e = cudaStreamEndCapture(cs, &graph);
+            }
+            if (e == cudaSuccess) e = cudaGraphInstantiate(&b->graph, graph, 0);
+            if (graph) cudaGraphDestroy(graph);
+            cudaStreamDestroy(cs);
+            if (e != cudaSuccess) {
+                b->graph = nullptr;
+                return bcuda(b, e, "capturing the batch step graph");
+            }
+            b->graph_ntiles = b->ntiles;
+        }
+        while (max_steps - done >= G) {
+            e = cudaGraphLaunch(b->graph, b->stream);
+            if (e != cudaSuccess) return bcuda(b, e, "launching the batch step graph");
+            b->launches += G;
+            done += G;
+        }
+    }
+    if (done < max_steps) {
+        e = launch_steps(0, max_steps - done);
+        if (e != cudaSuccess) return bcuda(b, e, "launching the batch kernel");
+        b->launches += max_steps - done;
+    }
+    for (size_t i = 0; i < nm; ++i) {
+        Member& m = b->members[i];
+        if (!m.used) continue;
+        const int k = steps_of[i];
+        m.t += k;
+        m.cur ^= (k & 1);
+        if (m.steps_left >= 0) m.steps_left -= k;
+    }
+    return FHP_OK;
+}
+
+int fhp_batch_synchronize(fhp_batch* b) {
+    if (!b) return bfail(nullptr, FHP_EINVAL, "batch is NULL");
+    DeviceGuard dg(b->device);
+    cudaError_t e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return bcuda(b, e, "synchronizing");
+    unsigned int word = 0;
+    e = cudaMemcpy(&word, b->d_err, sizeof word, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return bcuda(b, e, "reading the error word");
+    if (word) {
+        cudaMemset(b->d_err, 0, sizeof word);
+        return bfail(b, FHP_ETIMEOUT, "a batch kernel gave up waiting for its input copies");
+    }
+    return FHP_OK;
+}
+
+int32_t fhp_batch_count(const fhp_batch* b) {
+    if (!b) return -1;
+    int32_t n = 0;
+    for (const auto& m : b->members) n += m.used ? 1 : 0;
+    return n;
+}
+
+size_t fhp_batch_free_bytes(const fhp_batch* b) { return b ? b->arena.free_bytes() : 0; }
+
+int64_t fhp_batch_kernel_launches(const fhp_batch* b) { return b ? b->launches : -1; }
+
+}  // extern "C"

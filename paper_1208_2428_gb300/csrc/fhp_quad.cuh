@@ -162,5 +162,94 @@ __device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32
         : "memory");
 }
 
+// Stage layout: slot k (plane k for k < 7, the solid plane for k = 7) holds
+// R rows of Pq words; staged row r of every slot feeds output row y0 + r, so
+// slots 3, 4 hold source rows y0 + r - 1 and slots 0, 1 rows y0 + r + 1.
+template <bool SOLID>
+__device__ void issue_tile(const StepArgs& a, const TileArgs& ta, const uint32_t* src, int tile,
+                           uint32_t* stage, uint64_t* bar) {
+    constexpr int NP = SOLID ? 8 : 7;
+    const int y0 = tile * ta.R;
+    const int rows = min(ta.R, a.H - y0);
+    const uint32_t row_bytes = (uint32_t)a.Pq * 4u;
+    mbar_arrive_expect_tx(bar, (uint32_t)NP * (uint32_t)rows * row_bytes);
+#pragma unroll
+    for (int slot = 0; slot < NP; ++slot) {
+        const uint32_t* plane = slot < 7 ? src + (size_t)slot * a.plane_words : a.solid;
+        const int shift = (slot == 3 || slot == 4) ? -1 : (slot == 0 || slot == 1) ? 1 : 0;
+        int r = 0;
+        while (r < rows) {
+            int yy = y0 + shift + r;
+            if (yy < 0) yy += a.H;
+            if (yy >= a.H) yy -= a.H;
+            const int run = min(rows - r, a.H - yy);  // contiguous rows up to the end of the plane
+            bulk_copy_g2s(stage + ((size_t)slot * ta.R + r) * a.Pq, plane + (size_t)yy * a.Pq,
+                          (uint32_t)run * row_bytes, bar);
+            r += run;
+        }
+    }
+}
+
+template <bool SOLID, bool FORCE, bool RAGGED>
+__device__ __forceinline__ void quad_from_stage(const StepArgs& a, const StepVar& v, const TileArgs& ta,
+                                                const uint32_t* stage, int r, int y, int q) {
+    const int Pq = a.Pq, R = ta.R;
+    const int w = 4 * q;
+    const int m = RAGGED ? (q == a.nq - 1 ? a.Wq - w : 4) : 4;
+    const int wl = q == 0 ? a.Wq - 1 : w - 1;       // word left of the quad (periodic)
+    const int wr = q == a.nq - 1 ? 0 : w + 4;       // word right of the quad (periodic)
+    const uint32_t* s0 = stage + (size_t)r * Pq;    // slot 0, row r
+    const size_t slot = (size_t)R * Pq;
+    const uint4 i0 = ld4(s0 + 0 * slot + w), i1 = ld4(s0 + 1 * slot + w);
+    const uint4 i2 = ld4(s0 + 2 * slot + w), i3 = ld4(s0 + 3 * slot + w);
+    const uint4 i4 = ld4(s0 + 4 * slot + w), i5 = ld4(s0 + 5 * slot + w);
+    const uint4 i6 = ld4(s0 + 6 * slot + w);
+    uint4 sd = make_uint4(0u, 0u, 0u, 0u);
+    if (SOLID) sd = ld4(s0 + 7 * slot + w);
+    uint4 n0, n1, n2, n3, n4, n5;
+    if ((y & 1) == 0) {
+        // Even row: E, NE, SE come from x-1; W from x+1; NW, SW from x.
+        n2 = pull_left(i2, s0[2 * slot + wl]);
+        n3 = pull_left(i3, s0[3 * slot + wl]);
+        n1 = pull_left(i1, s0[1 * slot + wl]);
+        n5 = pull_right<RAGGED>(i5, s0[5 * slot + wr], m);
+        n4 = i4;
+        n0 = i0;
+    } else {
+        // Odd row: E from x-1; W, NW, SW from x+1; NE, SE from x.
+        n2 = pull_left(i2, s0[2 * slot + wl]);
+        n5 = pull_right<RAGGED>(i5, s0[5 * slot + wr], m);
+        n4 = pull_right<RAGGED>(i4, s0[4 * slot + wr], m);
+        n0 = pull_right<RAGGED>(i0, s0[0 * slot + wr], m);
+        n3 = i3;
+        n1 = i1;
+    }
+    finish_quad<SOLID, FORCE, RAGGED>(a, v, q, y, m, n0, n1, n2, n3, n4, n5, i6, sd, true);
+}
+
+template <bool SOLID, bool FORCE, bool RAGGED>
+__device__ __forceinline__ void compute_tile(const StepArgs& a, const StepVar& v, const TileArgs& ta, int tile,
+                                             const uint32_t* stage, int tid, int nthreads) {
+    const int y0 = tile * ta.R;
+    const int rows = min(ta.R, a.H - y0);
+    // Items ordered even local rows first, then odd ones, so that the row
+    // parity (which selects the shift pattern) is uniform within a warp.
+    const int even_rows = (rows + 1) >> 1;
+    const int even_items = even_rows * a.nq;
+    const int items = rows * a.nq;
+    for (int it = tid; it < items; it += nthreads) {
+        const int h = it >= even_items;
+        const uint32_t j = (uint32_t)(h ? it - even_items : it);
+        const int k = (int)(((unsigned long long)j * ta.nq_magic) >> 32);  // j / nq
+        const int q = (int)j - k * a.nq;
+        const int r = 2 * k + h;
+        quad_from_stage<SOLID, FORCE, RAGGED>(a, v, ta, stage, r, y0 + r, q);
+    }
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
 }  // namespace
 }  // namespace fhp

@@ -77,6 +77,26 @@ def load(path: str | None = None):
         "fhp_get_step_kernel": (ctypes.c_int, [vp]),
         "fhp_kernel_launches": (i64, [vp]),
         "fhp_philox4x32_10_device": (ctypes.c_int, [vp, vp, vp, i64, vp]),
+        "fhp_batch_lattice_bytes": (ctypes.c_size_t, [i32, i32]),
+        "fhp_batch_create": (ctypes.c_int, [ctypes.POINTER(vp), ctypes.c_size_t, vp, vp]),
+        "fhp_batch_destroy": (None, [vp]),
+        "fhp_batch_last_error": (ctypes.c_char_p, [vp]),
+        "fhp_batch_add": (ctypes.c_int, [vp, i32, i32, ctypes.c_uint64, ctypes.c_double,
+                                         ctypes.POINTER(ctypes.c_int32)]),
+        "fhp_batch_remove": (ctypes.c_int, [vp, i32]),
+        "fhp_batch_set_state": (ctypes.c_int, [vp, i32, u8p]),
+        "fhp_batch_get_state": (ctypes.c_int, [vp, i32, u8p]),
+        "fhp_batch_set_time": (ctypes.c_int, [vp, i32, i64]),
+        "fhp_batch_get_time": (i64, [vp, i32]),
+        "fhp_batch_set_steps_left": (ctypes.c_int, [vp, i32, i64]),
+        "fhp_batch_get_steps_left": (i64, [vp, i32]),
+        "fhp_batch_step": (ctypes.c_int, [vp, i64]),
+        "fhp_batch_set_graph_steps": (ctypes.c_int, [vp, i32]),
+        "fhp_batch_coarse_grain": (ctypes.c_int, [vp, i32, i32, vp, vp, vp, vp]),
+        "fhp_batch_synchronize": (ctypes.c_int, [vp]),
+        "fhp_batch_count": (i32, [vp]),
+        "fhp_batch_free_bytes": (ctypes.c_size_t, [vp]),
+        "fhp_batch_kernel_launches": (i64, [vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -261,6 +281,125 @@ class Lattice:
             self._h, int(block), ctypes.c_void_p(counts.data_ptr()), ctypes.c_void_p(rho.data_ptr()),
             ctypes.c_void_p(ux.data_ptr()), ctypes.c_void_p(uy.data_ptr())))
         return counts, rho, ux, uy
+
+
+class Batch:
+    """Many independent FHP lattices advanced by shared kernel launches.
+
+    Members are added and removed while the batch lives (continuous
+    batching); each keeps its own seed, forcing probability, obstacles, step
+    counter and optional step budget, and evolves exactly as it would alone.
+    The batch's device arena is a torch allocation of ``arena_bytes``.
+    """
+
+    def __init__(self, arena_bytes: int, device=None, stream=None):
+        torch = _torch()
+        self._lib = load()
+        self.device = torch.device("cuda", torch.cuda.current_device()) if device is None \
+            else torch.device(device)
+        with torch.cuda.device(self.device):
+            self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+            self._mem = torch.empty(int(arena_bytes) + 256, dtype=torch.uint8, device=self.device)
+            aligned = (self._mem.data_ptr() + 255) & ~255
+            h = ctypes.c_void_p()
+            rc = self._lib.fhp_batch_create(ctypes.byref(h), int(arena_bytes), ctypes.c_void_p(aligned),
+                                            ctypes.c_void_p(self.stream.cuda_stream))
+        if rc != FHP_OK:
+            raise FhpError(rc, self._lib.fhp_last_error(None).decode())
+        self._h = h
+        self.shapes = {}
+
+    def _check(self, rc: int):
+        if rc != FHP_OK:
+            raise FhpError(rc, self._lib.fhp_batch_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.fhp_batch_destroy(self._h)
+            self._h = None
+            self._mem = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @staticmethod
+    def lattice_bytes(width: int, height: int) -> int:
+        return int(load().fhp_batch_lattice_bytes(int(width), int(height)))
+
+    def add(self, width: int, height: int, seed: int = 0, forcing_p: float = 0.0) -> int:
+        slot = ctypes.c_int32(-1)
+        self._check(self._lib.fhp_batch_add(self._h, int(width), int(height), int(seed) & (2**64 - 1),
+                                            float(forcing_p), ctypes.byref(slot)))
+        self.shapes[slot.value] = (int(height), int(width))
+        return slot.value
+
+    def remove(self, slot: int):
+        self._check(self._lib.fhp_batch_remove(self._h, int(slot)))
+        self.shapes.pop(int(slot), None)
+
+    def set_state(self, slot: int, state: np.ndarray):
+        s = np.ascontiguousarray(state, dtype=np.uint8)
+        if s.shape != self.shapes[slot]:
+            raise ValueError(f"state must be {self.shapes[slot]}")
+        self._check(self._lib.fhp_batch_set_state(self._h, int(slot), _ptr(s)))
+
+    def get_state(self, slot: int) -> np.ndarray:
+        out = np.empty(self.shapes[slot], dtype=np.uint8)
+        self._check(self._lib.fhp_batch_get_state(self._h, int(slot), _ptr(out)))
+        return out
+
+    def set_time(self, slot: int, t: int):
+        self._check(self._lib.fhp_batch_set_time(self._h, int(slot), int(t)))
+
+    def time(self, slot: int) -> int:
+        return int(self._lib.fhp_batch_get_time(self._h, int(slot)))
+
+    def set_steps_left(self, slot: int, n: int):
+        self._check(self._lib.fhp_batch_set_steps_left(self._h, int(slot), int(n)))
+
+    def steps_left(self, slot: int) -> int:
+        return int(self._lib.fhp_batch_get_steps_left(self._h, int(slot)))
+
+    def step(self, n: int = 1):
+        self._check(self._lib.fhp_batch_step(self._h, int(n)))
+
+    def set_graph_steps(self, n: int):
+        self._check(self._lib.fhp_batch_set_graph_steps(self._h, int(n)))
+
+    def coarse_grain(self, slot: int, block: int = 32):
+        H, W = self.shapes[slot]
+        nby, nbx = H // block, W // block
+        counts = np.empty((nby, nbx, 9), dtype=np.int32)
+        rho = np.empty((nby, nbx), dtype=np.float32)
+        ux = np.empty_like(rho)
+        uy = np.empty_like(rho)
+        self._check(self._lib.fhp_batch_coarse_grain(self._h, int(slot), int(block), _ptr(counts), _ptr(rho),
+                                                     _ptr(ux), _ptr(uy)))
+        return counts, rho, ux, uy
+
+    def synchronize(self):
+        self._check(self._lib.fhp_batch_synchronize(self._h))
+
+    @property
+    def count(self) -> int:
+        return int(self._lib.fhp_batch_count(self._h))
+
+    @property
+    def free_bytes(self) -> int:
+        return int(self._lib.fhp_batch_free_bytes(self._h))
+
+    @property
+    def kernel_launches(self) -> int:
+        return int(self._lib.fhp_batch_kernel_launches(self._h))
 
 
 def philox4x32_10_device(ctr, key, stream=None):

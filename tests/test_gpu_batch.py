@@ -1,0 +1,128 @@
+"""Batches of independent lattices (shared launches, continuous membership):
+every member must equal the CPU oracle run of that lattice alone, bit-exact."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1208_2428_gb300 import build as cuda_build
+    cuda_build.build()
+    import paper_1208_2428_gb300 as p
+    p.load()
+    return p
+
+
+def small_ensemble(n, seed, sides=range(128, 641, 64), force_every=3):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    jobs = []
+    for i in range(n):
+        W, H = int(rng.choice(list(sides))), int(rng.choice(list(sides)))
+        p = 0.05 if i % force_every == 0 else 0.0
+        jobs.append(workloads.Lattice(f"m{i}", W, H, float(rng.uniform(0.1, 0.5)), 9000 + i, p, 0,
+                                      obstacle="points", point_frac=0.01))
+    return jobs
+
+
+def oracle_alone(oracle_mod, job, s0, t0, n):
+    out, _ = oracle_mod.run(s0, job.seed, t0, n, job.p)
+    return out
+
+
+def test_batch_matches_oracle(pkg, oracle_mod):
+    jobs = small_ensemble(24, 1)
+    states = [j.initial_state() for j in jobs]
+    arena = sum(pkg.Batch.lattice_bytes(j.W, j.H) for j in jobs) + (64 << 20)
+    with pkg.Batch(arena) as b:
+        b.set_graph_steps(8)
+        slots = []
+        for j, s0 in zip(jobs, states):
+            k = b.add(j.W, j.H, j.seed, j.p)
+            b.set_state(k, s0)
+            b.set_time(k, 3)
+            slots.append(k)
+        b.step(37)                       # 4 graph replays of 8 steps + 5 direct launches
+        b.synchronize()
+        for j, s0, k in zip(jobs, states, slots):
+            assert b.time(k) == 40
+            want = oracle_alone(oracle_mod, j, s0, 3, 37)
+            got = b.get_state(k)
+            assert np.array_equal(got, want), (j.name, j.W, j.H, int((got != want).sum()))
+
+
+def test_batch_continuous_membership_and_budgets(pkg, oracle_mod):
+    """Members join, leave and carry different step budgets; each one's
+    result equals its run alone."""
+    jobs = small_ensemble(12, 2)
+    states = [j.initial_state() for j in jobs]
+    arena = sum(pkg.Batch.lattice_bytes(j.W, j.H) for j in jobs) + (64 << 20)
+    with pkg.Batch(arena) as b:
+        b.set_graph_steps(4)
+        slot = {}
+        steps_done = {}
+        # first wave
+        for i in range(6):
+            slot[i] = b.add(jobs[i].W, jobs[i].H, jobs[i].seed, jobs[i].p)
+            b.set_state(slot[i], states[i])
+            b.set_steps_left(slot[i], [7, 11, 3, 20, 20, 9][i])
+        b.step(10)
+        for i in range(6):
+            steps_done[i] = min(10, [7, 11, 3, 20, 20, 9][i])
+        # members 2 and 5 finished and leave; check them now
+        for i in (2, 5):
+            got = b.get_state(slot[i])
+            assert np.array_equal(got, oracle_alone(oracle_mod, jobs[i], states[i], 0, steps_done[i])), i
+            b.remove(slot[i])
+        # second wave joins (slots are reused)
+        for i in range(6, 12):
+            slot[i] = b.add(jobs[i].W, jobs[i].H, jobs[i].seed, jobs[i].p)
+            b.set_state(slot[i], states[i])
+            steps_done[i] = 0
+        b.step(13)
+        for i in (0, 1, 3, 4):
+            budget = [7, 11, 3, 20, 20, 9][i]
+            steps_done[i] = min(budget, steps_done[i] + 13)
+        for i in range(6, 12):
+            steps_done[i] = 13
+        for i in list(range(6)) + list(range(6, 12)):
+            if i in (2, 5):
+                continue
+            got = b.get_state(slot[i])
+            want = oracle_alone(oracle_mod, jobs[i], states[i], 0, steps_done[i])
+            assert np.array_equal(got, want), (i, steps_done[i])
+            assert b.time(slot[i]) == steps_done[i]
+
+
+def test_batch_coarse_grain_and_arena_limits(pkg, oracle_mod):
+    job = workloads.Lattice("cg", 256, 192, 0.3, 77, 0.01, 0, obstacle="walls")
+    s0 = job.initial_state()
+    need = pkg.Batch.lattice_bytes(job.W, job.H)
+    with pkg.Batch(4 * need) as b:
+        k = b.add(job.W, job.H, job.seed, job.p)
+        extra = []
+        with pytest.raises(pkg.FhpError) as ei:   # admission control: the arena fills up
+            for _ in range(8):
+                extra.append(b.add(job.W, job.H, 1, 0.0))
+        assert ei.value.code == 2                 # FHP_ENOMEM
+        assert 1 <= len(extra) <= 3
+        for e in extra:
+            b.remove(e)
+        b.set_state(k, s0)
+        b.step(9)
+        counts, rho, ux, uy = b.coarse_grain(k, 64)
+        want = oracle_alone(oracle_mod, job, s0, 0, 9)
+        c_ref, rho_ref, _, _ = oracle_mod.coarse_grain(want, 64)
+        assert np.array_equal(counts, c_ref)
+        np.testing.assert_allclose(rho, rho_ref.astype(np.float32), rtol=1e-6)
+        b.remove(k)
+        k2 = b.add(job.W, job.H, 1, 0.0)          # memory came back
+        assert b.count == 1 and k2 == k
