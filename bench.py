@@ -44,8 +44,11 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=40, help="timed benchmark steps")
     ap.add_argument("--warmup", type=int, default=3, help="untimed warm-up benchmark steps")
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
-    ap.add_argument("--workload", choices=["cylinder", "channel", "periodic", "paper", "cylinder2x"],
+    ap.add_argument("--workload", choices=["cylinder", "channel", "periodic", "paper", "cylinder2x", "ensemble"],
                     default="cylinder")
+    ap.add_argument("--ensemble-size", type=int, default=512, help="lattices of the ensemble workload")
+    ap.add_argument("--no-batch-compare", action="store_true",
+                    help="skip the reduced batched-vs-per-lattice comparison of the default run")
     ap.add_argument("--lattice-steps", type=int, default=None,
                     help="time steps per benchmark step (default: the workload's run length)")
     ap.add_argument("--temporal-block", type=int, default=1)
@@ -185,6 +188,94 @@ def cpu_baseline(job, s0, target_seconds: float):
     return {"value": job.W * job.H * n / dt / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{n} whole-lattice time steps of the {job.W}x{job.H} workload "
                       f"({job.W * job.H * n:.3g} site updates, {dt:.1f} s, OpenMP row strips)"}
+
+
+def batched_vs_per_lattice(dev, stream, count: int, steps: int, per_steps: int, repeats: int = 1):
+    """Aggregate GSUPS of `count` ensemble lattices (sides 128..2048, 1 %
+    point obstacles, per-lattice seeds and densities) advanced (a) as one
+    batch -- one launch per step over all lattices, CUDA-graph replays -- and
+    (b) lattice by lattice, each with its own launches."""
+    import torch
+    import workloads
+    from paper_1208_2428_gb300 import Batch, Lattice
+    jobs = workloads.ensemble_512(count)
+    states = [j.initial_state() for j in jobs]
+    nodes = sum(j.nodes for j in jobs)
+    arena = sum(Batch.lattice_bytes(j.W, j.H) for j in jobs) + (256 << 20)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with Batch(arena, device=dev, stream=stream) as b:
+        b.set_graph_steps(64)
+        for j, s0 in zip(jobs, states):
+            k = b.add(j.W, j.H, j.seed, j.p)
+            b.set_state(k, s0)
+        b.step(64)
+        b.synchronize()
+        best = None
+        for _ in range(repeats):
+            l0 = b.kernel_launches
+            ev0.record(stream)
+            b.step(steps)
+            ev1.record(stream)
+            torch.cuda.synchronize(dev)
+            ms = ev0.elapsed_time(ev1)
+            best = ms if best is None else min(best, ms)
+            launches_batched = b.kernel_launches - l0
+    batched = nodes * steps / (best / 1e3) / 1e9
+    lats = []
+    for j, s0 in zip(jobs, states):
+        lat = Lattice(j.W, j.H, seed=j.seed, forcing_p=j.p, device=dev, stream=stream)
+        lat.set_state(s0)
+        lats.append(lat)
+    for lat in lats:
+        lat.step(2)
+    torch.cuda.synchronize(dev)
+    l0 = sum(lat.kernel_launches for lat in lats)
+    ev0.record(stream)
+    for lat in lats:
+        lat.step(per_steps)
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms_per = ev0.elapsed_time(ev1)
+    launches_per = sum(lat.kernel_launches for lat in lats) - l0
+    for lat in lats:
+        lat.close()
+    per = nodes * per_steps / (ms_per / 1e3) / 1e9
+    return {"lattices": count, "nodes": nodes, "batched_gsups": batched, "batched_steps": steps,
+            "batched_launches": launches_batched, "per_lattice_gsups": per, "per_lattice_steps": per_steps,
+            "per_lattice_launches": launches_per, "speedup": batched / per,
+            "batched_ms": best, "per_lattice_ms": ms_per}
+
+
+def run_ensemble(args):
+    """The 512-lattice ensemble: the batched path is the timed metric."""
+    import torch
+    world, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    steps = args.lattice_steps or 2000
+    sampler = ClockSampler(local)
+    sampler.start()
+    r = batched_vs_per_lattice(dev, stream, args.ensemble_size, steps, min(steps, 200), repeats=max(1, args.steps))
+    clocks = sampler.stop()
+    peak, peak_src = measured_hbm_peak()
+    bytes_per_node = 15 / 8.0
+    achieved = r["batched_gsups"] * 1e9 * bytes_per_node / 1e9
+    line = {
+        "metric": METRIC, "value": r["batched_gsups"], "unit": UNIT, "n_gpus": 1, "steps": max(1, args.steps),
+        "warmup": args.warmup, "ms_per_step": r["batched_ms"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u32 (bit-planes, boolean/integer)",
+        "data": "synthetic (512 seeded lattices, sides uniform in 128..2048 step 64, 1 % point obstacles)",
+        "config": {"workload": f"ensemble_{args.ensemble_size}", "lattice_steps_per_step": steps,
+                   "graph_steps": 64, "l2": "inputs (1.1 GB) larger than L2"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": None, "kernel": "fhp_batch_kernel", "algorithmic_bytes_per_node_step": bytes_per_node,
+                     "peak_source": peak_src},
+        "batched_vs_per_lattice": r, "cpu_baseline": None, "e2e": None,
+        "gpu_launches": r["batched_launches"], "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
 
 
 def run_reference(args):
@@ -360,6 +451,10 @@ def run_gpu(args):
                "d2h_bytes_per_step": int(h_counts.nbytes + h_rho.nbytes + h_ux.nbytes + h_uy.nbytes) if B else 0,
                "steps": e2e_steps}
 
+    batch_cmp = None
+    if rank == 0 and not args.no_batch_compare and args.workload == "cylinder":
+        batch_cmp = batched_vs_per_lattice(dev, stream, 64, 200, 200)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(job, s0, args.cpu_seconds)
@@ -386,6 +481,7 @@ def run_gpu(args):
                          "peak_source": peak_src},
             "cpu_baseline": cpu,
             "e2e": e2e,
+            "batched_vs_per_lattice": batch_cmp,
             "gpu_launches": launches,
             "clocks": clocks,
         }
@@ -400,6 +496,8 @@ def main():
     args = parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "ensemble":
+        return run_ensemble(args)
     return run_gpu(args)
 
 
