@@ -71,6 +71,9 @@ def _load():
         lib.oracle_coarse_grain.argtypes = [ctypes.c_int, ctypes.c_int, u8p, ctypes.c_int,
                                             i32p, f64p, f64p, f64p]
         lib.oracle_coarse_grain.restype = None
+        lib.oracle_init_random.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_uint64, ctypes.c_double,
+                                           u8p, u8p]
+        lib.oracle_init_random.restype = None
         lib.oracle_set_threads.argtypes = [ctypes.c_int]
         lib.oracle_set_threads.restype = None
         lib.oracle_max_threads.argtypes = []
@@ -148,6 +151,19 @@ def coarse_grain(state: np.ndarray, B: int):
                                 _ptr(counts, ctypes.c_int32), _ptr(rho, ctypes.c_double),
                                 _ptr(ux, ctypes.c_double), _ptr(uy, ctypes.c_double))
     return counts, rho, ux, uy
+
+
+def init_random(W: int, H: int, seed: int, density: float, solid=None) -> np.ndarray:
+    """Generated initial state (each of bits 0..6 of a fluid node set with
+    probability round(density * 2^16) / 2^16 from counter-based draws)."""
+    out = np.empty((H, W), dtype=np.uint8)
+    mask = None
+    if solid is not None:
+        mask = np.ascontiguousarray(solid, dtype=np.uint8)
+    _load().oracle_init_random(int(W), int(H), int(seed), float(density),
+                               _ptr(mask, ctypes.c_uint8) if mask is not None else None,
+                               _ptr(out, ctypes.c_uint8))
+    return out
 
 
 def set_threads(n: int) -> None:

@@ -335,6 +335,52 @@ ORACLE_EXPORT void oracle_coarse_grain(int W, int H, const uint8_t* state, int B
     }
 }
 
+/* ------------------------------------------------------------------------ */
+/* Random initial state (reading R-init2, used when the state is generated  */
+/* rather than uploaded): bit b (0..6) of fluid node x in row y is set iff  */
+/* its 16-bit uniform is below P = round-half-even(rho * 2^16).  The        */
+/* uniforms of word w = x / 32 and bit b come from the Philox blocks with    */
+/* counter (w, y, b, j), j = 0..3, under the key (seed_lo ^ 0x9E3779B9,      */
+/* seed_hi ^ 0x7F4A7C15) -- a key of its own, so these draws never meet the  */
+/* step's.  Node i = x mod 32 of the word takes block j = i / 8, output      */
+/* word (i mod 8) / 2, half i mod 2 (low 16 bits for even i).  Solid nodes   */
+/* (mask nonzero) get bit 7 only.                                            */
+/* ------------------------------------------------------------------------ */
+ORACLE_EXPORT void oracle_init_random(int W, int H, uint64_t seed, double rho, const uint8_t* solid_mask,
+                                      uint8_t* state) {
+    double scaled = rho * 65536.0;
+    uint32_t P;
+    if (!(scaled > 0.0)) P = 0;
+    else if (scaled >= 65536.0) P = 65536;
+    else {
+        uint32_t fl = (uint32_t)scaled;
+        double frac = scaled - (double)fl;
+        if (frac > 0.5 || (frac == 0.5 && (fl & 1))) fl += 1;
+        P = fl;
+    }
+    const uint32_t key[2] = {(uint32_t)seed ^ 0x9E3779B9u, (uint32_t)(seed >> 32) ^ 0x7F4A7C15u};
+#pragma omp parallel for schedule(static)
+    for (int y = 0; y < H; ++y) {
+        for (int x = 0; x < W; ++x) {
+            uint8_t v = 0;
+            if (solid_mask && solid_mask[(size_t)y * W + x]) {
+                v = 0x80;
+            } else {
+                int i = x & 31;
+                for (int b = 0; b < 7; ++b) {
+                    uint32_t ctr[4] = {(uint32_t)(x >> 5), (uint32_t)y, (uint32_t)b, (uint32_t)(i >> 3)};
+                    uint32_t out[4];
+                    oracle_philox4x32_10(ctr, key, out);
+                    uint32_t word = out[(i & 7) >> 1];
+                    uint32_t u = (i & 1) ? (word >> 16) : (word & 0xFFFFu);
+                    if (u < P) v |= (uint8_t)(1u << b);
+                }
+            }
+            state[(size_t)y * W + x] = v;
+        }
+    }
+}
+
 ORACLE_EXPORT void oracle_set_threads(int n) {
 #ifdef _OPENMP
     if (n > 0) omp_set_num_threads(n);

@@ -482,3 +482,43 @@ def test_coarse_grain_closed_forms(oracle_mod):
     assert ux[1, 1] == pytest.approx(-0.5) and rho[1, 1] == 2.0
     # the solid node is not counted: block (1,2) has one fluid node fewer and no particles
     assert counts[1, 2, 7] == B * B - 1 and counts[1, 2, 8] == 0
+
+
+# --------------------------------------------------------------------------
+# Generated initial state (reading R-init2)
+# --------------------------------------------------------------------------
+
+def test_init_random_closed_forms_and_statistics(oracle_mod):
+    W, H = 512, 64
+    empty = oracle_mod.init_random(W, H, 5, 0.0)
+    assert not empty.any()
+    full = oracle_mod.init_random(W, H, 5, 1.0)
+    assert np.all(full == 0x7F)
+    mask = np.zeros((H, W), dtype=bool)
+    mask[3, :] = True
+    mask[10:20, 100:140] = True
+    s = oracle_mod.init_random(W, H, 7, 0.3, mask)
+    assert np.all(s[mask] == 0x80) and not np.any(s[~mask] & 0x80)
+    # each bit set with probability round(0.3 * 65536) / 65536, independently
+    fluid = s[~mask]
+    p = round(0.3 * 65536) / 65536
+    n = fluid.size
+    sd = math.sqrt(p * (1 - p) / n)
+    for b in range(7):
+        assert abs(float(np.mean(fluid >> b & 1)) - p) < 5 * sd
+    # pairs of bits of one node are independent: P(both) = p^2
+    both = float(np.mean((fluid & 1) & (fluid >> 1 & 1)))
+    assert abs(both - p * p) < 5 * math.sqrt(p * p * (1 - p * p) / n)
+    # neighbouring nodes of a word are independent too
+    adj = float(np.mean((s[:, 0:W:2] & 1) & (s[:, 1:W:2] & 1)))
+    assert abs(adj - p * p) < 0.01
+    # the uniforms are the documented Philox outputs (key transform, counter, halves)
+    seed = 0x1234_5678_9ABC_DEF0
+    key = [(seed & 0xFFFFFFFF) ^ 0x9E3779B9, (seed >> 32) ^ 0x7F4A7C15]
+    x, y, b = 45, 6, 3
+    i = x % 32
+    blk = oracle_mod.philox4x32_10([x // 32, y, b, i // 8], key)
+    word = int(blk[(i % 8) // 2])
+    u = (word >> 16) if i % 2 else (word & 0xFFFF)
+    s2 = oracle_mod.init_random(W, H, seed, 0.5)
+    assert (int(s2[y, x]) >> b & 1) == (1 if u < 32768 else 0)
