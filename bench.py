@@ -44,9 +44,14 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=40, help="timed benchmark steps")
     ap.add_argument("--warmup", type=int, default=3, help="untimed warm-up benchmark steps")
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
-    ap.add_argument("--workload", choices=["cylinder", "channel", "periodic", "paper", "cylinder2x", "ensemble"],
+    ap.add_argument("--workload", choices=["cylinder", "channel", "periodic", "paper", "cylinder2x", "ensemble",
+                                           "serving"],
                     default="cylinder")
     ap.add_argument("--ensemble-size", type=int, default=512, help="lattices of the ensemble workload")
+    ap.add_argument("--serving-jobs", type=int, default=2000, help="requests of the serving trace")
+    ap.add_argument("--serving-budget-gb", type=float, default=80.0, help="HBM budget of the serving arena")
+    ap.add_argument("--no-serving-compare", action="store_true",
+                    help="skip the one-lattice-at-a-time replay of the serving trace")
     ap.add_argument("--no-batch-compare", action="store_true",
                     help="skip the reduced batched-vs-per-lattice comparison of the default run")
     ap.add_argument("--lattice-steps", type=int, default=None,
@@ -63,10 +68,16 @@ def parse_args():
 
 
 def workload(name: str):
+    """The single lattice a workload is timed on (for the batched workloads,
+    the CPU oracle's sample: the ensemble's first lattice, or the first
+    cylinder request of the serving trace)."""
     import workloads
     return {"cylinder": workloads.cylinder_16384x4096, "channel": workloads.channel_4096x1024,
             "periodic": workloads.periodic_256, "paper": workloads.cylinder_paper_size,
-            "cylinder2x": lambda: workloads.cylinder_scaled(16384, 8192)}[name]()
+            "cylinder2x": lambda: workloads.cylinder_scaled(16384, 8192),
+            "ensemble": lambda: workloads.ensemble_512()[0],
+            "serving": lambda: next(j for j in workloads.serving_jobs(50) if j.obstacle == "cylinder"),
+            }[name]()
 
 
 def measured_hbm_peak():
@@ -80,7 +91,8 @@ def measured_hbm_peak():
 
 def source_hash() -> str:
     h = hashlib.sha256()
-    for rel in ("paper_1208_2428_gb300/csrc/fhp_step.cu", "paper_1208_2428_gb300/csrc/fhp_device.cuh"):
+    for rel in ("paper_1208_2428_gb300/csrc/fhp_step.cu", "paper_1208_2428_gb300/csrc/fhp_device.cuh",
+                "paper_1208_2428_gb300/csrc/fhp_quad.cuh"):
         with open(os.path.join(ROOT, rel), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
@@ -278,6 +290,87 @@ def run_ensemble(args):
     return 0
 
 
+def serving_requests(count: int, time_scale: float = 1.0):
+    """The serving trace: Poisson arrivals (200/s), log-uniform sides and step
+    counts, half of the requests with the cylinder geometry and forcing."""
+    import workloads
+    from paper_1208_2428_gb300.serving import Request
+    reqs = []
+    for j in workloads.serving_jobs(count):
+        obst = (lambda W=j.W, H=j.H: workloads.cylinder_mask(W, H)) if j.obstacle == "cylinder" else None
+        reqs.append(Request(j.W, j.H, j.steps, seed=j.seed, density=j.density, forcing_p=j.p, obstacles=obst,
+                            cg_block=64, arrival=j.arrival * time_scale, name=j.name))
+    return reqs
+
+
+def serve_trace(dev, stream, reqs, budget_bytes: int, compare: bool):
+    """Serve a trace by continuous batching (and, optionally, one lattice at a
+    time); returns the summaries and the server's counters."""
+    from paper_1208_2428_gb300 import serving
+    with serving.Server(budget_bytes, quantum_max=64, quantum_min=8, graph_steps=16, device=dev, stream=stream,
+                        time_device=True) as srv:
+        done = srv.serve(reqs, realtime=True)
+        st = srv.stats
+    out = {"served": serving.summarize(done), "ticks": st.ticks, "peak_resident": st.peak_resident,
+           "peak_resident_gb": st.peak_resident_bytes / 1e9, "admissions_deferred": st.admissions_deferred,
+           "device_ms": st.device_ms, "device_launches": st.device_launches,
+           "issued_site_updates": st.issued_site_updates,
+           "issued_solid_site_updates": st.issued_solid_site_updates}
+    if compare:
+        out["one_lattice_at_a_time"] = serving.summarize(serving.serve_sequential(reqs, realtime=True, device=dev))
+    return out
+
+
+def run_serving(args):
+    """Serving: requests arrive (Poisson, 200/s) and are served by continuous
+    batching within an HBM budget; the metric is aggregate GSUPS over the
+    trace, with p50/p99 request latency."""
+    import torch
+    world, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    budget = int(args.serving_budget_gb * 1e9)
+    for _ in range(args.warmup):   # short traces: graph capture, allocator, clocks
+        serve_trace(dev, stream, serving_requests(40, 0.2), min(budget, 8 << 30), compare=False)
+    torch.cuda.synchronize(dev)
+    reqs = serving_requests(args.serving_jobs)
+    sampler = ClockSampler(local)
+    sampler.start()
+    r = serve_trace(dev, stream, reqs, budget, compare=not args.no_serving_compare)
+    clocks = sampler.stop()
+    peak, peak_src = measured_hbm_peak()
+    # Algorithmic bytes: 7 state bits read and written per node update, plus
+    # the solid bit where the lattice carries obstacles.
+    alg_bytes = r["issued_site_updates"] * 1.75 + r["issued_solid_site_updates"] * 0.125
+    achieved = alg_bytes / (r["device_ms"] / 1e3) / 1e9 if r["device_ms"] > 0 else 0.0
+    served = r["served"]
+    h2d = sum(q.width * q.height for q in reqs if q.obstacles is not None)
+    d2h = sum((q.width // q.cg_block) * (q.height // q.cg_block) * 48 for q in reqs)
+    value = served["gsups"]
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": 1, "warmup": args.warmup,
+        "ms_per_step": served["span_s"] * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u32 (bit-planes, boolean/integer)",
+        "data": f"synthetic serving trace ({len(reqs)} requests, Poisson 200/s, sides log-uniform 256..8192, "
+                "steps log-uniform 100..10000, half with a cylinder and forcing 5e-4)",
+        "config": {"workload": f"serving_{len(reqs)}", "hbm_budget_gb": args.serving_budget_gb,
+                   "quantum_steps": "8..64", "graph_steps": 16, "coarse_grain_block": 64,
+                   "l2": "inputs (resident lattices, GBs) larger than L2"},
+        "latency_ms": {"p50": served.get("p50_ms"), "p99": served.get("p99_ms"), "mean": served.get("mean_ms"),
+                       "max": served.get("max_ms")},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None, "kernel": "fhp_batch_kernel",
+                     "algorithmic_bytes": alg_bytes, "kernel_ms": r["device_ms"], "peak_source": peak_src},
+        "serving": r, "cpu_baseline": None,
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "note": "the serving metric is itself end to end: wall clock from arrival to result on the host"},
+        "gpu_launches": r["device_launches"], "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_reference(args):
     world, rank, _ = dist_setup()
     if rank != 0:
@@ -452,8 +545,16 @@ def run_gpu(args):
                "steps": e2e_steps}
 
     batch_cmp = None
+    serving_cmp = None
     if rank == 0 and not args.no_batch_compare and args.workload == "cylinder":
         batch_cmp = batched_vs_per_lattice(dev, stream, 64, 200, 200)
+        # A reduced serving trace (the first 300 requests, Poisson 200/s):
+        # continuous batching against one lattice at a time.
+        serving_cmp = serve_trace(dev, stream, serving_requests(300), int(args.serving_budget_gb * 1e9),
+                                  compare=True)
+        serving_cmp = {"requests": 300, "continuous_batching": serving_cmp["served"],
+                       "one_lattice_at_a_time": serving_cmp["one_lattice_at_a_time"],
+                       "peak_resident": serving_cmp["peak_resident"]}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -482,6 +583,7 @@ def run_gpu(args):
             "cpu_baseline": cpu,
             "e2e": e2e,
             "batched_vs_per_lattice": batch_cmp,
+            "serving_reduced": serving_cmp,
             "gpu_launches": launches,
             "clocks": clocks,
         }
@@ -498,6 +600,8 @@ def main():
         return run_reference(args)
     if args.workload == "ensemble":
         return run_ensemble(args)
+    if args.workload == "serving":
+        return run_serving(args)
     return run_gpu(args)
 
 

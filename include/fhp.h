@@ -103,6 +103,15 @@ FHP_API int fhp_get_state(fhp_lattice* lattice, uint8_t* host_bytes);
 FHP_API int fhp_set_state_device(fhp_lattice* lattice, const uint8_t* device_bytes);
 FHP_API int fhp_get_state_device(fhp_lattice* lattice, uint8_t* device_bytes);
 
+/* Replace the particles of every fluid node by a generated random state:
+ * each of bits 0..6 set independently with probability
+ * round(density * 2^16) / 2^16, drawn from Philox4x32-10 blocks with counter
+ * (x / 32, y, bit, j) under the lattice seed's init key (seed halves xored
+ * with 0x9E3779B9 and 0x7F4A7C15); node i = x mod 32 of a word takes block
+ * j = i / 8, output word (i mod 8) / 2, the low 16 bits for even i.  Solid
+ * nodes (load obstacles first) end empty.  Asynchronous. */
+FHP_API int fhp_init_random(fhp_lattice* lattice, double density);
+
 /* Replace the solid map from an H x W host mask (nonzero = solid) and clear
  * the particles of every node that is solid in the new map (paper Section 2:
  * boundary nodes carry bit 7 and reflect particles).  Synchronous. */
@@ -220,6 +229,15 @@ FHP_API int fhp_batch_add(fhp_batch* batch, int32_t width, int32_t height, uint6
 /* Remove a member and return its memory to the arena (waits for queued work). */
 FHP_API int fhp_batch_remove(fhp_batch* batch, int32_t slot);
 
+/* Generated initial state of a member (as fhp_init_random). */
+FHP_API int fhp_batch_init_random(fhp_batch* batch, int32_t slot, double density);
+/* Obstacles of a member (as fhp_load_obstacles), H x W bytes, nonzero =
+ * solid.  Asynchronous: the mask is copied on the batch's stream; a pageable
+ * buffer may be reused on return, a page-locked one only after
+ * fhp_batch_synchronize.  FHP_ENOMEM if the arena has no room for the H x W
+ * staging bytes. */
+FHP_API int fhp_batch_load_obstacles(fhp_batch* batch, int32_t slot, const uint8_t* host_mask);
+
 /* Member state as H x W node bytes (as fhp_set_state / fhp_get_state). */
 FHP_API int fhp_batch_set_state(fhp_batch* batch, int32_t slot, const uint8_t* host_bytes);
 FHP_API int fhp_batch_get_state(fhp_batch* batch, int32_t slot, uint8_t* host_bytes);
@@ -234,7 +252,10 @@ FHP_API int64_t fhp_batch_get_steps_left(const fhp_batch* batch, int32_t slot);
 /* Advance every member by min(n, its budget) steps.  Asynchronous. */
 FHP_API int fhp_batch_step(fhp_batch* batch, int64_t n);
 
-/* Steps per captured CUDA graph of batch launches (0: launch directly). */
+/* Steps per captured CUDA graph of batch launches (0: launch directly).  The
+ * graph reads the tile list and its length from device memory, so it is
+ * captured once and survives members joining and leaving (it is captured
+ * again only when the descriptor tables grow). */
 FHP_API int fhp_batch_set_graph_steps(fhp_batch* batch, int32_t steps);
 
 /* Coarse-grain one member into host buffers (as fhp_coarse_grain). */

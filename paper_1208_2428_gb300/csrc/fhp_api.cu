@@ -289,6 +289,17 @@ int fhp_load_obstacles(fhp_lattice* h, const uint8_t* host_mask) {
     return read_solid_flag(h);
 }
 
+int fhp_init_random(fhp_lattice* h, double density) {
+    if (!h) return fail(nullptr, FHP_EINVAL, "lattice is NULL");
+    if (!(density >= 0.0 && density <= 1.0)) return fail(h, FHP_EINVAL, "density %g outside [0, 1]", density);
+    DeviceGuard dg(h->device);
+    cudaError_t e = fhp::launch_init_random(h->g, h->buf[h->cur], h->solid, h->has_solid, h->seed, density,
+                                            h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "launching the init kernel");
+    ++h->launches;
+    return FHP_OK;
+}
+
 int fhp_step(fhp_lattice* h, int64_t n) {
     if (!h) return fail(nullptr, FHP_EINVAL, "lattice is NULL");
     if (n < 0) return fail(h, FHP_EINVAL, "negative step count %lld", (long long)n);

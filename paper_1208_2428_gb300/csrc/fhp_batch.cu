@@ -77,7 +77,7 @@ __device__ __forceinline__ void batch_compute(const StageHeader& h, const uint32
 }
 
 __global__ void __launch_bounds__(kBThreads, 2)
-    fhp_batch_kernel(const BatchLattice* __restrict__ lats, const BatchTile* __restrict__ tiles, int ntiles,
+    fhp_batch_kernel(const BatchLattice* __restrict__ lats, const BatchTile* __restrict__ tiles,
                      const int* __restrict__ step_base, int step_offset, unsigned int* err) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw);
@@ -86,8 +86,12 @@ __global__ void __launch_bounds__(kBThreads, 2)
     uint32_t* stages = reinterpret_cast<uint32_t*>(smem_raw + kBPrefixBytes);
     const int stage_words = kBStageBudget / 4;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int count = (ntiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
-    const int s = *step_base + step_offset;  // step index within the current call
+    // step_base[0]: steps of the current call already done by earlier graph
+    // replays; step_base[1]: number of tiles.  Both live in device memory so
+    // that a captured graph stays valid when members join or leave.
+    const int ntiles = step_base[1];
+    const int count = ntiles > (int)blockIdx.x ? (ntiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x : 0;
+    const int s = step_base[0] + step_offset;  // step index within the current call
 
     if (threadIdx.x == 0) {
         for (int k = 0; k < kBStages; ++k) {
@@ -275,9 +279,9 @@ struct fhp_batch {
     std::vector<fhp::BatchTile> h_tiles;
     bool tiles_dirty = true;
     int ntiles = 0;
+    int h_counters[2] = {0, 0};                 // source of the step_base upload
     int graph_steps = 64;
     cudaGraphExec_t graph = nullptr;
-    int graph_ntiles = -1;
     int64_t launches = 0;
     std::string err;
 };
@@ -307,7 +311,6 @@ Member* member(fhp_batch* b, int32_t slot) {
 void drop_graph(fhp_batch* b) {
     if (b->graph) cudaGraphExecDestroy(b->graph);
     b->graph = nullptr;
-    b->graph_ntiles = -1;
 }
 
 // Make sure the device tables can hold `lats` lattices and `tiles` tiles.
@@ -497,6 +500,41 @@ int fhp_batch_set_state(fhp_batch* b, int32_t slot, const uint8_t* host_bytes) {
     return FHP_OK;
 }
 
+int fhp_batch_init_random(fhp_batch* b, int32_t slot, double density) {
+    Member* m = member(b, slot);
+    if (!m || !(density >= 0.0 && density <= 1.0)) return bfail(b, FHP_EINVAL, "invalid slot %d or density", slot);
+    DeviceGuard dg(b->device);
+    cudaError_t e = fhp::launch_init_random(m->g, m->buf[m->cur], m->solid, m->has_solid, m->seed, density, b->stream);
+    if (e != cudaSuccess) return bcuda(b, e, "launching the init kernel");
+    ++b->launches;
+    return FHP_OK;
+}
+
+int fhp_batch_load_obstacles(fhp_batch* b, int32_t slot, const uint8_t* host_mask) {
+    Member* m = member(b, slot);
+    if (!m || !host_mask) return bfail(b, FHP_EINVAL, "invalid slot %d or NULL mask", slot);
+    DeviceGuard dg(b->device);
+    const size_t n = (size_t)m->g.W * m->g.H;
+    size_t off;
+    int rc = scratch_bytes_op(b, n, &off);
+    if (rc != FHP_OK) return rc;
+    uint8_t* staging = b->arena_base + off;
+    // Whether any node is solid is decided on the host, so the call does not
+    // wait for the device.  The staging block goes back to the arena at once:
+    // everything that could reuse it is ordered after the obstacle kernel on
+    // the batch's stream.
+    bool any = false;
+    for (size_t i = 0; i < n && !any; ++i) any = host_mask[i] != 0;
+    cudaError_t e = cudaMemcpyAsync(staging, host_mask, n, cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess)
+        e = fhp::launch_load_obstacles(m->g, staging, m->buf[m->cur], m->solid, m->flags, b->stream);
+    b->arena.release(off, n);
+    if (e != cudaSuccess) return bcuda(b, e, "loading a member's obstacles");
+    ++b->launches;
+    m->has_solid = any;
+    return FHP_OK;
+}
+
 int fhp_batch_get_state(fhp_batch* b, int32_t slot, uint8_t* host_bytes) {
     Member* m = member(b, slot);
     if (!m || !host_bytes) return bfail(b, FHP_EINVAL, "invalid slot %d or NULL bytes", slot);
@@ -609,7 +647,6 @@ int fhp_batch_step(fhp_batch* b, int64_t n) {
         if (e != cudaSuccess) return bcuda(b, e, "uploading the tile list");
         b->ntiles = (int)b->h_tiles.size();
         b->tiles_dirty = false;
-        drop_graph(b);
     }
     rc = ensure_tables(b, std::max<size_t>(nm, 1), std::max<size_t>(b->h_tiles.size(), 1));
     if (rc != FHP_OK) return rc;
@@ -648,18 +685,25 @@ int fhp_batch_step(fhp_batch* b, int64_t n) {
     }
     cudaError_t e = cudaMemcpyAsync(b->d_lats, b->h_lats.data(), nm * sizeof(fhp::BatchLattice),
                                     cudaMemcpyHostToDevice, b->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_step_base, 0, sizeof(int), b->stream);
+    b->h_counters[0] = 0;
+    b->h_counters[1] = b->ntiles;
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->d_step_base, b->h_counters, sizeof b->h_counters, cudaMemcpyHostToDevice, b->stream);
     if (e != cudaSuccess) return bcuda(b, e, "uploading the descriptors");
     int bps = fhp::batch_blocks_per_sm(b->device, &e);
     if (e != cudaSuccess) return bcuda(b, e, "configuring the batch kernel");
     int sms = 0;
     e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
     if (e != cudaSuccess) return bcuda(b, e, "querying the SM count");
-    const int grid = std::min(b->ntiles, bps * sms);
+    // Direct launches size the grid to the tile count; the graph is captured
+    // once with one resident wave of CTAs (those without a tile exit at once)
+    // and stays valid while the membership changes.
+    const int full_grid = bps * sms;
+    const int grid = std::min(b->ntiles, full_grid);
     const size_t smem = fhp::kBPrefixBytes + fhp::kBStages * fhp::kBStageBudget;
     auto launch_steps = [&](int first, int count) -> cudaError_t {
         for (int o = first; o < first + count; ++o) {
-            fhp::fhp_batch_kernel<<<grid, fhp::kBThreads, smem, b->stream>>>(b->d_lats, b->d_tiles, b->ntiles,
+            fhp::fhp_batch_kernel<<<grid, fhp::kBThreads, smem, b->stream>>>(b->d_lats, b->d_tiles,
                                                                               b->d_step_base, o, b->d_err);
             cudaError_t le = cudaGetLastError();
             if (le != cudaSuccess) return le;
@@ -669,7 +713,7 @@ int fhp_batch_step(fhp_batch* b, int64_t n) {
     int done = 0;
     const int G = b->graph_steps;
     if (G > 0 && max_steps >= G) {
-        if (!b->graph || b->graph_ntiles != b->ntiles) {
+        if (!b->graph) {
             drop_graph(b);
             cudaStream_t cs;
             e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
@@ -678,8 +722,8 @@ int fhp_batch_step(fhp_batch* b, int64_t n) {
             e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
             if (e == cudaSuccess) {
                 for (int o = 0; o < G; ++o)
-                    fhp::fhp_batch_kernel<<<grid, fhp::kBThreads, smem, cs>>>(b->d_lats, b->d_tiles, b->ntiles,
-                                                                               b->d_step_base, o, b->d_err);
+                    fhp::fhp_batch_kernel<<<full_grid, fhp::kBThreads, smem, cs>>>(b->d_lats, b->d_tiles,
+                                                                                    b->d_step_base, o, b->d_err);
                 fhp::advance_kernel<<<1, 32, 0, cs>>>(b->d_step_base, G);
                 e = cudaStreamEndCapture(cs, &graph);
             }
@@ -690,7 +734,6 @@ int fhp_batch_step(fhp_batch* b, int64_t n) {
                 b->graph = nullptr;
                 return bcuda(b, e, "capturing the batch step graph");
             }
-            b->graph_ntiles = b->ntiles;
         }
         while (max_steps - done >= G) {
             e = cudaGraphLaunch(b->graph, b->stream);

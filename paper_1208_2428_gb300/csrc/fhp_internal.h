@@ -103,6 +103,12 @@ cudaError_t launch_block(const Geometry& g, const uint32_t* src, uint32_t* dst, 
 cudaError_t launch_pack(const Geometry& g, const uint8_t* bytes, uint32_t* state,
                         uint32_t* solid, unsigned int* device_any_solid, cudaStream_t stream);
 
+// Generated initial state: bits 0..6 of every fluid node set independently
+// with probability round(density * 2^16) / 2^16 from counter-based draws of
+// the lattice seed (solid nodes end empty).
+cudaError_t launch_init_random(const Geometry& g, uint32_t* state, const uint32_t* solid, bool has_solid,
+                               uint64_t seed, double density, cudaStream_t stream);
+
 // Unpack 7 state planes + the solid plane into H x W node bytes (device).
 cudaError_t launch_unpack(const Geometry& g, const uint32_t* state, const uint32_t* solid,
                           uint8_t* bytes, cudaStream_t stream);

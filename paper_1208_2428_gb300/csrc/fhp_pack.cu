@@ -2,6 +2,9 @@
 // Fig. 1: bits 0-5 movers, bit 6 rest, bit 7 solid) and bit-planes, and the
 // obstacle map.  One warp converts one 32-node word at a time: lane j holds
 // node 32w + j and __ballot_sync gathers bit b of the 32 nodes into plane b.
+#include <cmath>
+
+#include "fhp_device.cuh"
 #include "fhp_internal.h"
 
 namespace fhp {
@@ -85,7 +88,55 @@ __global__ void __launch_bounds__(kBlock) obstacle_kernel(Geometry g, const uint
     }
 }
 
+// Generated initial state: for word w of row y and bit b, four Philox blocks
+// (counter (w, y, b, j), j = 0..3, under the init key) give the 32 nodes'
+// 16-bit uniforms -- node i takes block i / 8, output word (i mod 8) / 2,
+// half i mod 2 -- and the node's bit b is set iff its uniform < P.  Solid
+// nodes end without particles.
+__global__ void __launch_bounds__(kBlock) init_kernel(Geometry g, uint32_t* __restrict__ state,
+                                                      const uint32_t* __restrict__ solid, bool has_solid,
+                                                      Key2 key, uint32_t P) {
+    const size_t total = (size_t)g.H * g.Pq;
+    for (size_t item = (size_t)blockIdx.x * blockDim.x + threadIdx.x; item < total;
+         item += (size_t)gridDim.x * blockDim.x) {
+        const int y = (int)(item / g.Pq);
+        const int w = (int)(item - (size_t)y * g.Pq);
+        const size_t off = (size_t)y * g.Pq + w;
+        if (w >= g.Wq) {
+            for (int b = 0; b < 7; ++b) state[(size_t)b * g.plane_words + off] = 0u;
+            continue;
+        }
+        const uint32_t fluid = has_solid ? ~solid[off] : 0xFFFFFFFFu;
+        for (int b = 0; b < 7; ++b) {
+            uint32_t word = 0;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const uint4 r = philox4x32_10(make_uint4((uint32_t)w, (uint32_t)y, (uint32_t)b, (uint32_t)j), key);
+                const uint32_t outs[4] = {r.x, r.y, r.z, r.w};
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    const uint32_t u = (k & 1) ? (outs[k >> 1] >> 16) : (outs[k >> 1] & 0xFFFFu);
+                    word |= (u < P ? 1u : 0u) << (8 * j + k);
+                }
+            }
+            state[(size_t)b * g.plane_words + off] = word & fluid;
+        }
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_init_random(const Geometry& g, uint32_t* state, const uint32_t* solid, bool has_solid,
+                               uint64_t seed, double density, cudaStream_t stream) {
+    const double scaled = density * 65536.0;
+    uint32_t P;
+    if (!(scaled > 0.0)) P = 0;
+    else if (scaled >= 65536.0) P = 65536;
+    else P = (uint32_t)std::nearbyint(scaled);  // nearest, ties to even
+    const Key2 key{(uint32_t)seed ^ 0x9E3779B9u, (uint32_t)(seed >> 32) ^ 0x7F4A7C15u};
+    init_kernel<<<grid_for((size_t)g.H * g.Pq / 32 + 1), kBlock, 0, stream>>>(g, state, solid, has_solid, key, P);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_pack(const Geometry& g, const uint8_t* bytes, uint32_t* state, uint32_t* solid,
                         unsigned int* device_any_solid, cudaStream_t stream) {

@@ -77,6 +77,9 @@ def load(path: str | None = None):
         "fhp_get_step_kernel": (ctypes.c_int, [vp]),
         "fhp_kernel_launches": (i64, [vp]),
         "fhp_philox4x32_10_device": (ctypes.c_int, [vp, vp, vp, i64, vp]),
+        "fhp_init_random": (ctypes.c_int, [vp, ctypes.c_double]),
+        "fhp_batch_init_random": (ctypes.c_int, [vp, i32, ctypes.c_double]),
+        "fhp_batch_load_obstacles": (ctypes.c_int, [vp, i32, u8p]),
         "fhp_batch_lattice_bytes": (ctypes.c_size_t, [i32, i32]),
         "fhp_batch_create": (ctypes.c_int, [ctypes.POINTER(vp), ctypes.c_size_t, vp, vp]),
         "fhp_batch_destroy": (None, [vp]),
@@ -213,6 +216,10 @@ class Lattice:
         if m.shape != self.shape:
             raise ValueError(f"mask must be {self.shape}")
         self._check(self._lib.fhp_load_obstacles(self._h, _ptr(m)))
+
+    def init_random(self, density: float):
+        """Generated Bernoulli(density) occupation of every fluid node."""
+        self._check(self._lib.fhp_init_random(self._h, float(density)))
 
     # -- dynamics -------------------------------------------------------------
     def step(self, n: int = 1):
@@ -351,6 +358,15 @@ class Batch:
         if s.shape != self.shapes[slot]:
             raise ValueError(f"state must be {self.shapes[slot]}")
         self._check(self._lib.fhp_batch_set_state(self._h, int(slot), _ptr(s)))
+
+    def init_random(self, slot: int, density: float):
+        self._check(self._lib.fhp_batch_init_random(self._h, int(slot), float(density)))
+
+    def load_obstacles(self, slot: int, mask: np.ndarray):
+        m = np.ascontiguousarray(mask).astype(np.uint8, copy=False)
+        if m.shape != self.shapes[slot]:
+            raise ValueError(f"mask must be {self.shapes[slot]}")
+        self._check(self._lib.fhp_batch_load_obstacles(self._h, int(slot), _ptr(m)))
 
     def get_state(self, slot: int) -> np.ndarray:
         out = np.empty(self.shapes[slot], dtype=np.uint8)
