@@ -152,13 +152,55 @@ FHP_API int fhp_set_forcing(fhp_lattice* lattice, double p);
 
 /* Number of steps fused into one kernel pass (temporal blocking): 1, 2, 4
  * or 8.  With k > 1, fhp_step runs passes that stage a tile of the lattice
- * plus a k-row (and one 128-node) halo in shared memory and apply k steps
- * there before writing the tile back, so HBM is read and written once per k
- * steps; leftover steps (n mod k) and lattices the blocked kernel does not
- * support (W not a multiple of 128, fewer than 512 nodes per row, or
- * H < 2k + 2) use the single-step kernels.  Results are identical for every
- * value.  Default 1. */
+ * plus a halo of k rows and k words (forcing couples the 32 nodes of a word)
+ * in shared memory and apply k steps there before writing the tile back, so
+ * HBM is read and written once per k steps; leftover steps (n mod k) and
+ * lattices the blocked kernel does not support (W not a multiple of 128,
+ * fewer than 512 nodes per row, or H < 2k + 2) use the single-step kernels.
+ * Results are identical for every value.  Default 1. */
 FHP_API int fhp_set_temporal_block(fhp_lattice* lattice, int32_t k);
+
+/* Row-strip decomposition of one lattice across devices (the paper's
+ * multi-GPU runs, Table 1).  A strip is a lattice of its own whose array row
+ * y is row row_base + y of the whole lattice: the row keys the random words,
+ * so the strip's steps draw the whole lattice's chirality and forcing bits.
+ * The strip still wraps periodically in its own rows; a caller keeps g ghost
+ * rows above and below the rows it owns, refreshes them from the neighbouring
+ * strips (fhp_get_rows_device / fhp_set_rows_device), and then advances at
+ * most g steps, after which exactly the owned rows are exact.  row_base must
+ * be even (odd rows keep their half-cell shift); default 0. */
+FHP_API int fhp_set_row_offset(fhp_lattice* lattice, int32_t row_base);
+
+/* Row pitch in 32-bit words (32 nodes per word, rows padded to 4 words), or
+ * -1 for a NULL lattice. */
+FHP_API int32_t fhp_row_pitch_words(const fhp_lattice* lattice);
+
+/* Copy rows [y0, y0 + n) of the 7 state bit-planes to / from a device buffer
+ * laid out [plane 0..6][row][word] (7 * n * pitch words, pitch from
+ * fhp_row_pitch_words; padding words of a row are zero).  Asynchronous on the
+ * lattice's stream; the buffer is the caller's and must stay valid until the
+ * stream passes the copy.  FHP_EINVAL if the rows are outside the lattice. */
+FHP_API int fhp_get_rows_device(fhp_lattice* lattice, int32_t y0, int32_t n, uint32_t* device_words);
+FHP_API int fhp_set_rows_device(fhp_lattice* lattice, int32_t y0, int32_t n, const uint32_t* device_words);
+
+/* Temporal block fhp_step will use (1 if blocking is off or unsupported for
+ * this lattice), or -1 for a NULL lattice. */
+FHP_API int fhp_get_temporal_block(const fhp_lattice* lattice);
+
+/* Autotuner.  Times every step configuration that applies to this lattice --
+ * direct, ring and multi-step kernels, and temporal blocks k = 2, 4, 8 --
+ * over trial_steps steps each (a multiple of 8 in [8, 4096]; each candidate
+ * runs once untimed, then timed with CUDA events on the lattice's stream) and
+ * records the fastest for this device, lattice shape, and whether the
+ * lattice has obstacles and forcing.  From then on every lattice of that
+ * description whose settings are automatic (kernel 0, temporal block 1) runs
+ * the recorded configuration.  The state and the step counter are those of
+ * the call on return (the trials run from a saved copy of the state, which
+ * takes a temporary device allocation of 7 planes).  Synchronous.  out_kernel
+ * and out_temporal_block (may be NULL) receive the choice.  Results of
+ * fhp_step are identical for every configuration. */
+FHP_API int fhp_autotune(fhp_lattice* lattice, int32_t trial_steps, int32_t* out_kernel,
+                         int32_t* out_temporal_block);
 
 /* Step kernel used by fhp_step: 0 = automatic (default), 1 = direct (one
  * 128-node quad per thread, operands loaded into registers), 2 = bulk-copy
@@ -166,9 +208,11 @@ FHP_API int fhp_set_temporal_block(fhp_lattice* lattice, int32_t k);
  * cp.async.bulk, one launch per step), 3 = multi-step ring (the ring kernel
  * running all steps of an fhp_step call in one cooperative launch, each tile
  * waiting only for the three tiles of the previous step it reads).  2 and 3
- * fall back to 1 when a row does not fit a stage; automatic picks 3 when the
- * lattice has at least two tiles per SM, else 1.  Results are identical for
- * every choice. */
+ * fall back to 1 when a row does not fit a stage; automatic picks 1 below
+ * two tiles per SM, 3 up to 24 tiles per SM and 2 above.  Results are identical for
+ * every choice.  While the kernel is automatic and the temporal block 1, a
+ * configuration recorded by fhp_autotune for the lattice's description takes
+ * precedence. */
 FHP_API int fhp_set_step_kernel(fhp_lattice* lattice, int32_t kind);
 
 /* The step kernel fhp_step will run for the lattice's current settings
@@ -251,6 +295,30 @@ FHP_API int64_t fhp_batch_get_steps_left(const fhp_batch* batch, int32_t slot);
 
 /* Advance every member by min(n, its budget) steps.  Asynchronous. */
 FHP_API int fhp_batch_step(fhp_batch* batch, int64_t n);
+
+/* Batch step kernels.  SINGLE_STEP: one launch of the batch kernel per step
+ * (replayed from captured CUDA graphs, see fhp_batch_set_graph_steps).
+ * MULTI_STEP: all steps of an fhp_batch_step call in one cooperative launch;
+ * a tile is staged for step s once the tiles of step s - 1 it reads (itself
+ * and its two neighbours in its lattice) are finished, tracked by per-tile
+ * counters.  AUTO (default): autotuned online -- batches are classed by the
+ * binary order of magnitude of their tile count (fhp_batch_tile_count); the
+ * first call of at least 32 steps in a class runs half of its steps with each
+ * kernel, timed with CUDA events on the batch's stream, and a later call
+ * records the kernel with more node updates per millisecond for the class
+ * (read without waiting); until then SINGLE_STEP runs.  Results are
+ * identical for every choice. */
+#define FHP_BATCH_KERNEL_AUTO 0
+#define FHP_BATCH_KERNEL_SINGLE_STEP 1
+#define FHP_BATCH_KERNEL_MULTI_STEP 2
+FHP_API int fhp_batch_set_step_kernel(fhp_batch* batch, int32_t kind);
+FHP_API int fhp_batch_get_step_kernel(const fhp_batch* batch);
+/* The kernel AUTO has recorded for batches of `ntiles` tiles: 0 = not yet
+ * measured, else SINGLE_STEP or MULTI_STEP; -1 for invalid arguments. */
+FHP_API int fhp_batch_get_tuned_kernel(const fhp_batch* batch, int32_t ntiles);
+/* Number of row tiles of the current members (the unit of the batch
+ * kernels' work lists); -1 on error. */
+FHP_API int32_t fhp_batch_tile_count(fhp_batch* batch);
 
 /* Steps per captured CUDA graph of batch launches (0: launch directly).  The
  * graph reads the tile list and its length from device memory, so it is

@@ -68,6 +68,9 @@ def _load():
         lib.oracle_run.argtypes = [ctypes.c_int, ctypes.c_int, u8p, u8p, ctypes.c_uint64,
                                    ctypes.c_uint64, ctypes.c_int64, ctypes.c_double]
         lib.oracle_run.restype = ctypes.c_int64
+        lib.oracle_run_rows.argtypes = [ctypes.c_int, ctypes.c_int, u8p, u8p, ctypes.c_uint64, ctypes.c_uint64,
+                                        ctypes.c_int64, ctypes.c_double, ctypes.c_int64, ctypes.c_int]
+        lib.oracle_run_rows.restype = ctypes.c_int64
         lib.oracle_coarse_grain.argtypes = [ctypes.c_int, ctypes.c_int, u8p, ctypes.c_int,
                                             i32p, f64p, f64p, f64p]
         lib.oracle_coarse_grain.restype = None
@@ -134,6 +137,22 @@ def run(state: np.ndarray, seed: int, t0: int, n: int, p: float = 0.0) -> tuple[
     scratch = np.empty_like(s)
     ev = _load().oracle_run(W, H, _ptr(s, ctypes.c_uint8), _ptr(scratch, ctypes.c_uint8),
                             int(seed), int(t0), int(n), float(p))
+    return s, int(ev)
+
+
+def run_rows(rows: np.ndarray, seed: int, t0: int, n: int, p: float, row_base: int, global_height: int):
+    """Advance an h x W array whose row y is row (row_base + y) mod
+    global_height of a larger lattice, n steps, periodic in its own rows
+    (a strip with ghost rows: rows within n of its edges become invalid)."""
+    s = np.array(rows, dtype=np.uint8, order="C", copy=True)
+    H, W = s.shape
+    if W % 32 or W < 32 or H % 2 or H < 2 or row_base % 2:
+        raise ValueError("W must be a positive multiple of 32, H and row_base even")
+    scratch = np.empty_like(s)
+    ev = _load().oracle_run_rows(W, H, _ptr(s, ctypes.c_uint8), _ptr(scratch, ctypes.c_uint8), int(seed), int(t0),
+                                 int(n), float(p), int(row_base), int(global_height))
+    if ev < 0:
+        raise ValueError("invalid strip")
     return s, int(ev)
 
 

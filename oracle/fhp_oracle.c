@@ -244,13 +244,16 @@ static int force_word(uint8_t* row, int w, uint64_t seed, uint64_t t, int y,
 /* One time step (R-order): S_{t+1} = Force_t(Scatter_t(Move(S_t))).         */
 /* in and out are H x W bytes, row-major; they must not overlap.             */
 /* ------------------------------------------------------------------------ */
+/* Row y of the array is row (row_base + y) mod Hg of the lattice: that row
+ * keys the random words (for a whole lattice row_base = 0 and Hg = H).       */
 static int64_t step_once(int W, int H, const uint8_t* in, uint8_t* out, uint64_t seed,
                          uint64_t t, const uint64_t q[33], int force_on,
-                         const uint8_t table[2][256]) {
+                         const uint8_t table[2][256], int64_t row_base, int Hg) {
     int64_t events = 0;
 #pragma omp parallel for schedule(static) reduction(+ : events)
     for (int y = 0; y < H; ++y) {
         uint8_t* orow = out + (size_t)y * W;
+        const int gy = (int)((((row_base + y) % Hg) + Hg) % Hg);
         uint32_t chi_word = 0;
         for (int x = 0; x < W; ++x) {
             /* Motion: the particle moving along c_i that arrives at (x, y)
@@ -263,20 +266,41 @@ static int64_t step_once(int W, int H, const uint8_t* in, uint8_t* out, uint64_t
                 b |= in[(size_t)sy * W + sx] & dir_bit(i);
             }
             /* Scattering with this node's chirality bit (stream 0). */
-            if ((x & 31) == 0) chi_word = rng_word(seed, t, y, x >> 5, 0u);
+            if ((x & 31) == 0) chi_word = rng_word(seed, t, gy, x >> 5, 0u);
             int chi = (chi_word >> (x & 31)) & 1;
             orow[x] = table[chi][b];
         }
         if (force_on)
-            for (int w = 0; w < W / 32; ++w) events += force_word(orow, w, seed, t, y, q);
+            for (int w = 0; w < W / 32; ++w) events += force_word(orow, w, seed, t, gy, q);
     }
     return events;
 }
+
+static int64_t run_rows(int W, int H, uint8_t* state, uint8_t* scratch, uint64_t seed, uint64_t t0, int64_t n,
+                        double p, int64_t row_base, int Hg);
 
 /* Advance `state` (H x W bytes) by n steps starting at step t0.  `scratch`
  * must hold H x W bytes.  Returns the total number of forcing events. */
 ORACLE_EXPORT int64_t oracle_run(int W, int H, uint8_t* state, uint8_t* scratch, uint64_t seed,
                                  uint64_t t0, int64_t n, double p) {
+    return run_rows(W, H, state, scratch, seed, t0, n, p, 0, H);
+}
+
+/* A strip of a larger lattice, for the row-strip decomposition across
+ * devices (the paper's multi-GPU runs, Table 1): `state` holds H rows, row y
+ * being row (row_base + y) mod Hg of a W x Hg lattice, and is advanced n steps
+ * as if periodic in its own H rows.  Rows within n rows of either edge of
+ * the array are therefore not those of the lattice; the others are exact when
+ * the array's edge rows held the lattice's rows at the start.  row_base must
+ * be even (so that the half-cell shift of odd rows is the lattice's), H even. */
+ORACLE_EXPORT int64_t oracle_run_rows(int W, int H, uint8_t* state, uint8_t* scratch, uint64_t seed, uint64_t t0,
+                                      int64_t n, double p, int64_t row_base, int Hg) {
+    if ((row_base & 1) || (H & 1) || Hg < 2) return -1;
+    return run_rows(W, H, state, scratch, seed, t0, n, p, row_base, Hg);
+}
+
+static int64_t run_rows(int W, int H, uint8_t* state, uint8_t* scratch, uint64_t seed, uint64_t t0, int64_t n,
+                        double p, int64_t row_base, int Hg) {
     uint8_t table[2][256];
     oracle_build_table(0, table[0]);
     oracle_build_table(1, table[1]);
@@ -287,7 +311,7 @@ ORACLE_EXPORT int64_t oracle_run(int W, int H, uint8_t* state, uint8_t* scratch,
     uint8_t* a = state;
     uint8_t* b = scratch;
     for (int64_t k = 0; k < n; ++k) {
-        events += step_once(W, H, a, b, seed, t0 + (uint64_t)k, q, force_on, table);
+        events += step_once(W, H, a, b, seed, t0 + (uint64_t)k, q, force_on, table, row_base, Hg);
         uint8_t* tmp = a; a = b; b = tmp;
     }
     if (a != state) memcpy(state, a, (size_t)W * H);

@@ -9,8 +9,10 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
+#include <vector>
 
 #include "../../include/fhp.h"
 #include "fhp_internal.h"
@@ -45,6 +47,41 @@ namespace {
 
 constexpr int64_t kMaxTime = (int64_t)1 << 48;
 thread_local std::string g_create_error;
+
+// Autotuned step configurations, per device and lattice shape.
+struct TuneKey {
+    int device, W, H;
+    bool solid, force;
+    bool operator==(const TuneKey& o) const {
+        return device == o.device && W == o.W && H == o.H && solid == o.solid && force == o.force;
+    }
+};
+struct TuneChoice {
+    int kernel;   // fhp::StepKernel other than kStepAuto
+    int k;        // temporal block
+};
+std::mutex g_tune_mutex;
+std::vector<std::pair<TuneKey, TuneChoice>> g_tuned;
+
+bool tuned_choice(const TuneKey& key, TuneChoice* out) {
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    for (const auto& kv : g_tuned)
+        if (kv.first == key) {
+            *out = kv.second;
+            return true;
+        }
+    return false;
+}
+
+void record_tuned(const TuneKey& key, const TuneChoice& c) {
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    for (auto& kv : g_tuned)
+        if (kv.first == key) {
+            kv.second = c;
+            return;
+        }
+    g_tuned.emplace_back(key, c);
+}
 
 size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
@@ -115,6 +152,20 @@ struct DeviceGuard {
         if (prev >= 0) cudaSetDevice(prev);
     }
 };
+
+// Kernel and temporal block fhp_step uses: the lattice's own settings, or,
+// while they are automatic (kernel 0, k = 1), the configuration autotuned
+// for this shape if there is one.
+void effective_settings(const fhp_lattice* h, int* kernel, int* k_block) {
+    *kernel = h->step_kernel;
+    *k_block = h->k_block;
+    if (h->step_kernel != fhp::kStepAuto || h->k_block != 1) return;
+    TuneChoice c;
+    if (tuned_choice(TuneKey{h->device, h->g.W, h->g.H, h->has_solid, h->force}, &c)) {
+        *kernel = c.kernel;
+        *k_block = c.k;
+    }
+}
 
 int check_block(fhp_lattice* h, int32_t B) {
     if (B < 32 || B % 32 != 0 || h->g.W % B != 0 || h->g.H % B != 0)
@@ -306,9 +357,11 @@ int fhp_step(fhp_lattice* h, int64_t n) {
     if (n > kMaxTime - h->t) return fail(h, FHP_EINVAL, "step counter would pass 2^48");
     DeviceGuard dg(h->device);
     const fhp::Key2 key{(uint32_t)h->seed, (uint32_t)(h->seed >> 32)};
-    if (h->k_block > 1 && fhp::block_supported(h->g, h->k_block)) {
+    int kernel = h->step_kernel, k_block = h->k_block;
+    effective_settings(h, &kernel, &k_block);
+    if (k_block > 1 && fhp::block_supported(h->g, k_block)) {
         // Temporal blocking: passes of k steps; the remainder one step at a time.
-        const int k = h->k_block;
+        const int k = k_block;
         while (n >= k) {
             cudaError_t e = fhp::launch_block(h->g, h->buf[h->cur], h->buf[h->cur ^ 1], h->solid, h->has_solid,
                                               h->force, h->ft, key, (uint64_t)h->t, k, h->stream, h->flags + 1);
@@ -319,7 +372,7 @@ int fhp_step(fhp_lattice* h, int64_t n) {
             n -= k;
         }
     }
-    if (n >= 2 && fhp::resolved_step_kernel(h->g, h->has_solid, h->step_kernel) == fhp::kStepRun) {
+    if (n >= 2 && fhp::resolved_step_kernel(h->g, h->has_solid, kernel) == fhp::kStepRun) {
         // All n steps in cooperative launches of up to 2^24 steps each.
         int64_t left = n;
         while (left > 0) {
@@ -338,7 +391,7 @@ int fhp_step(fhp_lattice* h, int64_t n) {
     for (int64_t i = 0; i < n; ++i) {
         cudaError_t e = fhp::launch_step(h->g, h->buf[h->cur], h->buf[h->cur ^ 1], h->solid, h->has_solid,
                                          h->force, h->ft, key, (uint64_t)h->t, h->stream, h->flags + 1,
-                                         h->step_kernel);
+                                         kernel);
         if (e != cudaSuccess) return cuda_fail(h, e, "launching the step kernel");
         ++h->launches;
         h->cur ^= 1;
@@ -421,7 +474,145 @@ int fhp_set_step_kernel(fhp_lattice* h, int32_t kind) {
 int fhp_get_step_kernel(const fhp_lattice* h) {
     if (!h) return -1;
     DeviceGuard dg(h->device);
-    return fhp::resolved_step_kernel(h->g, h->has_solid, h->step_kernel);
+    int kernel, k_block;
+    effective_settings(h, &kernel, &k_block);
+    return fhp::resolved_step_kernel(h->g, h->has_solid, kernel);
+}
+
+int fhp_set_row_offset(fhp_lattice* h, int32_t row_base) {
+    if (!h) return fail(nullptr, FHP_EINVAL, "lattice is NULL");
+    if (row_base % 2) return fail(h, FHP_EINVAL, "row offset %d must be even", row_base);
+    h->g.row_base = row_base;
+    return FHP_OK;
+}
+
+int32_t fhp_row_pitch_words(const fhp_lattice* h) { return h ? h->g.Pq : -1; }
+
+namespace {
+// Rows [y0, y0 + n) of the 7 state planes to or from a packed device buffer
+// [plane][row][word] of 7 * n * Pq words.
+int copy_rows(fhp_lattice* h, int32_t y0, int32_t n, uint32_t* packed, bool to_lattice) {
+    if (!h) return fail(nullptr, FHP_EINVAL, "lattice is NULL");
+    if (!packed || y0 < 0 || n < 0 || (int64_t)y0 + n > h->g.H)
+        return fail(h, FHP_EINVAL, "rows [%d, %d) outside the lattice's %d rows or NULL buffer", y0, y0 + n, h->g.H);
+    if (n == 0) return FHP_OK;
+    DeviceGuard dg(h->device);
+    const size_t row_words = (size_t)h->g.Pq;
+    for (int p = 0; p < 7; ++p) {
+        uint32_t* plane = h->buf[h->cur] + (size_t)p * h->g.plane_words + (size_t)y0 * row_words;
+        uint32_t* buf = packed + (size_t)p * n * row_words;
+        cudaError_t e = to_lattice ? cudaMemcpyAsync(plane, buf, n * row_words * 4, cudaMemcpyDeviceToDevice, h->stream)
+                                   : cudaMemcpyAsync(buf, plane, n * row_words * 4, cudaMemcpyDeviceToDevice, h->stream);
+        if (e != cudaSuccess) return cuda_fail(h, e, "copying rows");
+    }
+    return FHP_OK;
+}
+}  // namespace
+
+int fhp_get_rows_device(fhp_lattice* h, int32_t y0, int32_t n, uint32_t* device_words) {
+    return copy_rows(h, y0, n, device_words, false);
+}
+
+int fhp_set_rows_device(fhp_lattice* h, int32_t y0, int32_t n, const uint32_t* device_words) {
+    return copy_rows(h, y0, n, const_cast<uint32_t*>(device_words), true);
+}
+
+int fhp_get_temporal_block(const fhp_lattice* h) {
+    if (!h) return -1;
+    int kernel, k_block;
+    effective_settings(h, &kernel, &k_block);
+    return k_block > 1 && fhp::block_supported(h->g, k_block) ? k_block : 1;
+}
+
+int fhp_autotune(fhp_lattice* h, int32_t trial_steps, int32_t* out_kernel, int32_t* out_temporal_block) {
+    if (!h) return fail(nullptr, FHP_EINVAL, "lattice is NULL");
+    if (trial_steps < 8 || trial_steps > 4096 || trial_steps % 8)
+        return fail(h, FHP_EINVAL, "trial_steps %d must be a multiple of 8 in [8, 4096]", trial_steps);
+    DeviceGuard dg(h->device);
+    int rc = fhp_synchronize(h);
+    if (rc != FHP_OK) return rc;
+    // The trials start from a saved copy of the state, restored afterwards.
+    const size_t state_bytes = (size_t)7 * h->g.plane_words * sizeof(uint32_t);
+    uint32_t* saved = nullptr;
+    cudaError_t e = cudaMalloc((void**)&saved, state_bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(h, FHP_ENOMEM, "autotune: no room for a copy of the state (%zu bytes)", state_bytes);
+    }
+    const int cur0 = h->cur;
+    const int64_t t0 = h->t;
+    const int kernel0 = h->step_kernel, k0 = h->k_block;
+    e = cudaMemcpyAsync(saved, h->buf[cur0], state_bytes, cudaMemcpyDeviceToDevice, h->stream);
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    if (e == cudaSuccess) e = cudaEventCreate(&ev[0]);
+    if (e == cudaSuccess) e = cudaEventCreate(&ev[1]);
+    std::vector<TuneChoice> cands;
+    cands.push_back({fhp::kStepDirect, 1});
+    if (fhp::resolved_step_kernel(h->g, h->has_solid, fhp::kStepRing) != fhp::kStepDirect) {
+        cands.push_back({fhp::kStepRing, 1});
+        cands.push_back({fhp::kStepRun, 1});
+    }
+    for (int k : {2, 4, 8})
+        if (fhp::block_supported(h->g, k) && trial_steps % k == 0) cands.push_back({fhp::kStepDirect, k});
+    TuneChoice best{fhp::kStepDirect, 1};
+    float best_ms = -1.0f;
+    for (size_t i = 0; e == cudaSuccess && i < cands.size(); ++i) {
+        h->step_kernel = cands[i].kernel;
+        h->k_block = cands[i].k;
+        // One untimed trial (first-use set-up), then the timed one.
+        rc = fhp_step(h, trial_steps);
+        if (rc == FHP_OK) rc = fhp_synchronize(h);
+        if (rc == FHP_OK) {
+            e = cudaEventRecord(ev[0], h->stream);
+            if (e == cudaSuccess) rc = fhp_step(h, trial_steps);
+            if (e == cudaSuccess && rc == FHP_OK) e = cudaEventRecord(ev[1], h->stream);
+            if (e == cudaSuccess && rc == FHP_OK) rc = fhp_synchronize(h);
+            float ms = 0.0f;
+            if (e == cudaSuccess && rc == FHP_OK) e = cudaEventElapsedTime(&ms, ev[0], ev[1]);
+            if (e == cudaSuccess && rc == FHP_OK && (best_ms < 0.0f || ms < best_ms)) {
+                best_ms = ms;
+                best = cands[i];
+            }
+        }
+        if (rc != FHP_OK || e != cudaSuccess) {
+            // A candidate that cannot launch is skipped; a failure the device
+            // reported (a wait that gave up, a sticky CUDA error) ends the tuning.
+            if (rc == FHP_ETIMEOUT) break;
+            cudaGetLastError();
+            const cudaError_t se = cudaStreamSynchronize(h->stream);
+            if (se != cudaSuccess) {
+                e = se;
+                break;
+            }
+            e = cudaSuccess;
+            rc = FHP_OK;
+        }
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(h->buf[cur0], saved, state_bytes, cudaMemcpyDeviceToDevice, h->stream);
+        h->cur = cur0;
+        h->t = t0;
+    }
+    if (e == cudaSuccess && rc == FHP_OK) e = cudaStreamSynchronize(h->stream);
+    for (cudaEvent_t x : ev)
+        if (x) cudaEventDestroy(x);
+    cudaFree(saved);
+    h->cur = cur0;
+    h->t = t0;
+    if (rc != FHP_OK || e != cudaSuccess || best_ms < 0.0f) {
+        h->step_kernel = kernel0;
+        h->k_block = k0;
+        if (rc != FHP_OK) return rc;
+        if (e != cudaSuccess) return cuda_fail(h, e, "autotuning");
+        return fail(h, FHP_ECUDA, "autotune: no step configuration ran");
+    }
+    // Keep the lattice automatic; the choice applies to every lattice of this
+    // shape (and obstacle / forcing flags) on this device.
+    h->step_kernel = fhp::kStepAuto;
+    h->k_block = 1;
+    record_tuned(TuneKey{h->device, h->g.W, h->g.H, h->has_solid, h->force}, best);
+    if (out_kernel) *out_kernel = best.kernel;
+    if (out_temporal_block) *out_temporal_block = best.k;
+    return FHP_OK;
 }
 
 int fhp_synchronize(fhp_lattice* h) {

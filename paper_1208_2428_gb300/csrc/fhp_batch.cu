@@ -36,7 +36,8 @@ namespace fhp {
 namespace {
 
 constexpr int kBConsumerWarps = 8;
-constexpr int kBThreads = (kBConsumerWarps + 1) * 32;
+constexpr int kBThreads = (kBConsumerWarps + 1) * 32;       // + producer warp
+constexpr int kBRunThreads = (kBConsumerWarps + 2) * 32;    // + producer and publisher warps
 constexpr int kBStages = 3;
 constexpr int kBStageBudget = 32 * 1024;
 
@@ -49,7 +50,7 @@ struct BatchLattice {
     int cur;                  // buffer holding S_{t0}
     int steps;                // steps in the current call (0: idle)
     int force;
-    int pad;
+    int tile_base;            // index of the lattice's tile 0 in the tile list
 };
 
 struct BatchTile {
@@ -68,7 +69,69 @@ struct __align__(16) StageHeader {
 };
 
 constexpr int kHeaderBytes = (int)((sizeof(StageHeader) + 127) / 128 * 128);
+constexpr int kDescWords = (int)(sizeof(StepArgs) / 4);
+constexpr int kDescRegs = (kDescWords + 31) / 32;
+static_assert(sizeof(StepArgs) % 4 == 0, "StepArgs is copied as 32-bit words");
 constexpr int kBPrefixBytes = 128 + kBStages * kHeaderBytes;  // barriers, then headers
+
+// Producer-side copy of one lattice's descriptor: word w of its StepArgs in
+// register w / 32 of lane w mod 32, the per-call fields in lane 0.
+struct DescCache {
+    int lat = -1;
+    uint32_t dw[kDescRegs];
+    int steps = 0, cur = 0, force = 0, tile_base = 0;
+    unsigned long long t0 = 0;
+    uint32_t* buf0 = nullptr;
+    uint32_t* buf1 = nullptr;
+    TileArgs ta{};
+};
+
+__device__ __forceinline__ void load_desc(DescCache& c, const BatchLattice* __restrict__ lats, int lat, int lane) {
+    const BatchLattice* L = lats + lat;
+    const uint32_t* srcw = reinterpret_cast<const uint32_t*>(&L->a);
+#pragma unroll
+    for (int j = 0; j < kDescRegs; ++j) {
+        const int w = lane + 32 * j;
+        c.dw[j] = w < kDescWords ? srcw[w] : 0u;
+    }
+    if (lane == 0) {
+        c.steps = L->steps;
+        c.cur = L->cur;
+        c.force = L->force;
+        c.tile_base = L->tile_base;
+        c.t0 = L->t0;
+        c.buf0 = L->buf[0];
+        c.buf1 = L->buf[1];
+        c.ta = L->ta;
+    }
+    c.lat = lat;
+}
+
+// All lanes write the descriptor words into the stage header, then lane 0
+// fills in the fields of step s and tile `tile`.
+__device__ __forceinline__ void write_header(StageHeader* h, const DescCache& c, int s, int tile, unsigned int* err,
+                                             int lane) {
+    uint32_t* dstw = reinterpret_cast<uint32_t*>(&h->a);
+#pragma unroll
+    for (int j = 0; j < kDescRegs; ++j) {
+        const int w = lane + 32 * j;
+        if (w < kDescWords) dstw[w] = c.dw[j];
+    }
+    __syncwarp();
+    if (lane == 0) {
+        const int par = (c.cur + s) & 1;
+        const unsigned long long t = c.t0 + (unsigned long long)s;
+        h->a.src = par ? c.buf1 : c.buf0;
+        h->a.dst = par ? c.buf0 : c.buf1;
+        h->a.t_lo = (uint32_t)t;
+        h->a.t_hi = (uint32_t)(t >> 32);
+        h->a.err = err;
+        h->ta = c.ta;
+        h->tile = tile;
+        h->active = s < c.steps;
+        h->force = c.force;
+    }
+}
 
 template <bool FORCE>
 __device__ __forceinline__ void batch_compute(const StageHeader& h, const uint32_t* stage) {
@@ -90,7 +153,10 @@ __global__ void __launch_bounds__(kBThreads, 2)
     // replays; step_base[1]: number of tiles.  Both live in device memory so
     // that a captured graph stays valid when members join or leave.
     const int ntiles = step_base[1];
-    const int count = ntiles > (int)blockIdx.x ? (ntiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x : 0;
+    // Each CTA takes a contiguous run of the tile list, so consecutive tiles
+    // mostly belong to the same lattice and its descriptor is loaded once.
+    const int first = (int)(((long long)blockIdx.x * ntiles) / gridDim.x);
+    const int count = (int)(((long long)(blockIdx.x + 1) * ntiles) / gridDim.x) - first;
     const int s = step_base[0] + step_offset;  // step index within the current call
 
     if (threadIdx.x == 0) {
@@ -103,10 +169,19 @@ __global__ void __launch_bounds__(kBThreads, 2)
     __syncthreads();
 
     if (warp == kBConsumerWarps) {
+        // The producer keeps the current lattice's descriptor in registers
+        // and reloads it only when the tile list moves on to another
+        // lattice; tile records are fetched 32 at a time.
         bool ok = true;
         int i = 0;
+        DescCache c;
+        BatchTile rec{0, 0};
         for (; i < count; ++i) {
             const int st = i % kBStages;
+            if ((i & 31) == 0 && i + lane < count) rec = tiles[first + i + lane];
+            const int bt_lat = __shfl_sync(0xFFFFFFFFu, rec.lattice, i & 31);
+            const int bt_tile = __shfl_sync(0xFFFFFFFFu, rec.tile, i & 31);
+            if (bt_lat != c.lat) load_desc(c, lats, bt_lat, lane);
             int waited = 1;
             if (lane == 0 && i >= kBStages)
                 waited = mbar_wait_bounded(&empty[st], (uint32_t)(((i / kBStages) - 1) & 1)) ? 1 : 0;
@@ -115,32 +190,12 @@ __global__ void __launch_bounds__(kBThreads, 2)
                 break;
             }
             __syncwarp();  // order lane 0's acquire of "empty" before the lanes rewrite the header
-            const BatchTile bt = tiles[blockIdx.x + i * gridDim.x];
-            const BatchLattice* L = lats + bt.lattice;
             StageHeader* h = headers + st;
-            // The lanes copy the lattice's StepArgs into the header.
-            {
-                const uint32_t* srcw = reinterpret_cast<const uint32_t*>(&L->a);
-                uint32_t* dstw = reinterpret_cast<uint32_t*>(&h->a);
-                for (int w = lane; w < (int)(sizeof(StepArgs) / 4); w += 32) dstw[w] = srcw[w];
-            }
-            __syncwarp();
+            write_header(h, c, s, bt_tile, err, lane);
             if (lane == 0) {
-                const int active = s < L->steps;
-                const int par = (L->cur + s) & 1;
-                const unsigned long long t = L->t0 + (unsigned long long)s;
-                h->a.src = L->buf[par];
-                h->a.dst = L->buf[par ^ 1];
-                h->a.t_lo = (uint32_t)t;
-                h->a.t_hi = (uint32_t)(t >> 32);
-                h->a.err = err;
-                h->ta = L->ta;
-                h->tile = bt.tile;
-                h->active = active;
-                h->force = L->force;
-                if (active) {
+                if (h->active) {
                     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                    issue_tile<true>(h->a, h->ta, h->a.src, bt.tile, stages + (size_t)st * stage_words, &full[st]);
+                    issue_tile<true>(h->a, h->ta, h->a.src, bt_tile, stages + (size_t)st * stage_words, &full[st]);
                 } else {
                     mbar_arrive_expect_tx(&full[st], 0u);  // nothing to stage: release the stage at once
                 }
@@ -171,6 +226,157 @@ __global__ void __launch_bounds__(kBThreads, 2)
     }
 }
 
+// All steps of a batch call in one cooperative launch.  As in the
+// single-lattice multi-step kernel, a tile may be staged for step s once the
+// tiles of the previous step whose rows it reads -- the tile and its two
+// neighbours within the same lattice (periodic in y) -- are finished: the
+// publisher warp bumps a tile's counter by kBConsumerWarps after one
+// GPU-scope fence when all consumer warps are done with it, and the producer
+// waits for the counters (bounded) before issuing the bulk copies.  Every
+// CTA handles its contiguous run of the tile list step after step, and all
+// CTAs are resident (cooperative launch), so every wait ends.  Members whose
+// budget ends within the call are skipped for the remaining steps.
+__global__ void __launch_bounds__(kBRunThreads, 2)
+    fhp_batch_run_kernel(const BatchLattice* __restrict__ lats, const BatchTile* __restrict__ tiles, int ntiles,
+                         int nsteps, unsigned int* __restrict__ done, unsigned int* err) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw);
+    uint64_t* empty = full + kBStages;
+    unsigned int* warp_done = reinterpret_cast<unsigned int*>(empty + kBStages);
+    StageHeader* headers = reinterpret_cast<StageHeader*>(smem_raw + 128);
+    uint32_t* stages = reinterpret_cast<uint32_t*>(smem_raw + kBPrefixBytes);
+    const int stage_words = kBStageBudget / 4;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // Item i of the CTA is tile list entry blockIdx.x + i * gridDim.x: the
+    // neighbours a tile waits for are handled at the same position by the
+    // neighbouring CTAs one step earlier, so the waits rarely stall.
+    const int first = (int)blockIdx.x;
+    const int stride = (int)gridDim.x;
+    const int count = ntiles > first ? (ntiles - first + stride - 1) / stride : 0;
+
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < kBStages; ++k) {
+            mbar_init(&full[k], 1);
+            mbar_init(&empty[k], kBConsumerWarps);
+        }
+        for (int w = 0; w < kBConsumerWarps; ++w) warp_done[w] = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+
+    if (warp == kBConsumerWarps + 1) {
+        // Publisher.
+        if (lane != 0) return;
+        const long long total = (long long)count * nsteps;
+        long long published = 0;
+        int i_next = 0;
+        unsigned long long start = 0;
+        while (published < total) {
+            unsigned int m = 0xFFFFFFFFu;
+            for (int w = 0; w < kBConsumerWarps; ++w) m = min(m, ld_acquire_cta_shared(&warp_done[w]));
+            if ((long long)m > published) {
+                asm volatile("fence.proxy.async.global;" ::: "memory");
+                asm volatile("fence.acq_rel.gpu;" ::: "memory");
+                for (; published < (long long)m; ++published) {
+                    atomicAdd(&done[first + i_next * stride], (unsigned int)kBConsumerWarps);
+                    if (++i_next == count) i_next = 0;
+                }
+                start = 0;
+                continue;
+            }
+            const unsigned long long now = global_ns();
+            if (start == 0) start = now;
+            else if (now - start > kWaitLimitNs) {
+                if (err) atomicOr(err, 1u);
+                return;
+            }
+            __nanosleep(64);
+        }
+        return;
+    }
+
+    if (warp == kBConsumerWarps) {
+        // Producer.
+        DescCache c;
+        BatchTile rec{0, 0};
+        bool ok = true;
+        long long k = 0;
+        for (int s = 0; ok && s < nsteps; ++s) {
+            const unsigned int target = (unsigned int)kBConsumerWarps * (unsigned int)s;
+            for (int i = 0; i < count; ++i) {
+                const int st = (int)(k % kBStages);
+                if ((i & 31) == 0 && i + lane < count) rec = tiles[first + (i + lane) * stride];
+                const int bt_lat = __shfl_sync(0xFFFFFFFFu, rec.lattice, i & 31);
+                const int bt_tile = __shfl_sync(0xFFFFFFFFu, rec.tile, i & 31);
+                if (bt_lat != c.lat) load_desc(c, lats, bt_lat, lane);
+                int good = 1;
+                if (lane == 0) {
+                    if (k >= kBStages) good = mbar_wait_bounded(&empty[st], (uint32_t)(((k / kBStages) - 1) & 1));
+                    if (good && s > 0 && s < c.steps) {
+                        // Rows of tiles prev, this and next of step s - 1.
+                        const int nt = c.ta.ntiles;
+                        const int g = c.tile_base + bt_tile;
+                        const int prev = c.tile_base + (bt_tile == 0 ? nt - 1 : bt_tile - 1);
+                        const int next = c.tile_base + (bt_tile == nt - 1 ? 0 : bt_tile + 1);
+                        good = wait_tiles(done, prev, next, g, true, target);
+                        // Written through the generic proxy by other CTAs; read
+                        // by the bulk copy through the async proxy.
+                        if (good) asm volatile("fence.proxy.async.global;" ::: "memory");
+                    }
+                }
+                if (!__shfl_sync(0xFFFFFFFFu, good, 0)) {
+                    ok = false;
+                    break;
+                }
+                __syncwarp();  // order lane 0's acquire of "empty" before the lanes rewrite the header
+                StageHeader* h = headers + st;
+                write_header(h, c, s, bt_tile, err, lane);
+                if (lane == 0) {
+                    if (h->active) {
+                        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                        issue_tile<true>(h->a, h->ta, h->a.src, bt_tile, stages + (size_t)st * stage_words,
+                                         &full[st]);
+                    } else {
+                        mbar_arrive_expect_tx(&full[st], 0u);
+                    }
+                }
+                __syncwarp();
+                ++k;
+            }
+        }
+        if (lane == 0) {
+            if (!ok && err) atomicOr(err, 1u);
+            // Never leave while copies into this CTA's shared memory may be in flight.
+            for (long long j = (k > kBStages ? k - kBStages : 0); j < k; ++j)
+                (void)mbar_wait_bounded(&full[j % kBStages], (uint32_t)((j / kBStages) & 1));
+        }
+        return;
+    }
+
+    // Consumers.
+    long long k = 0;
+    unsigned int finished = 0;
+    for (int s = 0; s < nsteps; ++s) {
+        for (int i = 0; i < count; ++i, ++k) {
+            const int st = (int)(k % kBStages);
+            if (!mbar_wait_bounded(&full[st], (uint32_t)((k / kBStages) & 1))) {
+                if (lane == 0 && err) atomicOr(err, 1u);
+                return;
+            }
+            const StageHeader& h = headers[st];
+            if (h.active) {
+                if (h.force) batch_compute<true>(h, stages + (size_t)st * stage_words);
+                else batch_compute<false>(h, stages + (size_t)st * stage_words);
+            }
+            __syncwarp();
+            if (lane == 0) {
+                mbar_arrive(&empty[st]);
+                st_release_cta_shared(&warp_done[warp], ++finished);
+            }
+        }
+    }
+}
+
 __global__ void advance_kernel(int* step_base, int by) {
     if (threadIdx.x == 0 && blockIdx.x == 0) *step_base += by;
 }
@@ -191,6 +397,31 @@ int batch_blocks_per_sm(int dev, cudaError_t* e) {
         *e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fhp_batch_kernel, kBThreads, smem);
         if (*e != cudaSuccess) return 0;
         cached[dev] = n > 0 ? n : 1;
+    }
+    *e = cudaSuccess;
+    return cached[dev];
+}
+
+int batch_run_blocks_per_sm(int dev, cudaError_t* e) {
+    static std::mutex m;
+    static int cached[64] = {};
+    std::lock_guard<std::mutex> lock(m);
+    if (dev < 0 || dev >= 64) {
+        *e = cudaErrorInvalidDevice;
+        return 0;
+    }
+    if (!cached[dev]) {
+        const int smem = kBPrefixBytes + kBStages * kBStageBudget;
+        *e = cudaFuncSetAttribute(fhp_batch_run_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (*e != cudaSuccess) return 0;
+        int n = 0;
+        *e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fhp_batch_run_kernel, kBRunThreads, smem);
+        if (*e != cudaSuccess) return 0;
+        if (n < 1) {
+            *e = cudaErrorInvalidConfiguration;
+            return 0;
+        }
+        cached[dev] = n;
     }
     *e = cudaSuccess;
     return cached[dev];
@@ -221,6 +452,7 @@ struct Member {
     int64_t steps_left = -1;      // -1: no budget
     bool has_solid = false;
     int R = 1;
+    int tile_base = 0;            // first entry of the member's tiles in the tile list
 };
 
 constexpr int64_t kMaxTime = (int64_t)1 << 48;
@@ -260,6 +492,15 @@ struct DeviceGuard {
 
 }  // namespace
 
+constexpr int kTuneClasses = 32;
+constexpr int kTuneMinSteps = 16;   // a trial runs at least this many steps with each kernel
+
+struct TuneTrial {
+    int cls = -1;                    // class being measured, -1: none in flight
+    cudaEvent_t ev[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // [single, multi][start, end]
+    double updates[2] = {0.0, 0.0};
+};
+
 struct fhp_batch {
     int device = 0;
     cudaStream_t stream = nullptr;
@@ -273,6 +514,10 @@ struct fhp_batch {
     size_t misc_off = SIZE_MAX;                 // step base + error word
     fhp::BatchLattice* d_lats = nullptr;
     fhp::BatchTile* d_tiles = nullptr;
+    unsigned int* d_done = nullptr;             // per-tile counters of the multi-step kernel
+    int step_kernel = FHP_BATCH_KERNEL_AUTO;
+    int tuned[kTuneClasses] = {};               // per tile-count class: kernel measured fastest (0: unknown)
+    TuneTrial trial;
     int* d_step_base = nullptr;
     unsigned int* d_err = nullptr;
     std::vector<fhp::BatchLattice> h_lats;
@@ -313,6 +558,10 @@ void drop_graph(fhp_batch* b) {
     b->graph = nullptr;
 }
 
+size_t tile_table_bytes(size_t cap) {
+    return fhp::round256(cap * sizeof(fhp::BatchTile)) + fhp::round256(cap * sizeof(unsigned int));
+}
+
 // Make sure the device tables can hold `lats` lattices and `tiles` tiles.
 int ensure_tables(fhp_batch* b, size_t lats, size_t tiles) {
     if (lats > b->lat_cap) {
@@ -326,13 +575,15 @@ int ensure_tables(fhp_batch* b, size_t lats, size_t tiles) {
         drop_graph(b);
     }
     if (tiles > b->tile_cap) {
+        // The tile list followed by one completion counter per tile.
         const size_t cap = std::max<size_t>(tiles, 2 * b->tile_cap + 256);
-        const size_t off = b->arena.allocate(cap * sizeof(fhp::BatchTile));
+        const size_t off = b->arena.allocate(tile_table_bytes(cap));
         if (off == SIZE_MAX) return bfail(b, FHP_ENOMEM, "batch arena full (tile table)");
-        if (b->tile_off != SIZE_MAX) b->arena.release(b->tile_off, b->tile_cap * sizeof(fhp::BatchTile));
+        if (b->tile_off != SIZE_MAX) b->arena.release(b->tile_off, tile_table_bytes(b->tile_cap));
         b->tile_off = off;
         b->tile_cap = cap;
         b->d_tiles = (fhp::BatchTile*)(b->arena_base + off);
+        b->d_done = (unsigned int*)(b->arena_base + off + fhp::round256(cap * sizeof(fhp::BatchTile)));
         drop_graph(b);
     }
     return FHP_OK;
@@ -414,6 +665,9 @@ void fhp_batch_destroy(fhp_batch* b) {
     DeviceGuard dg(b->device);
     cudaStreamSynchronize(b->stream);
     drop_graph(b);
+    for (auto& pair : b->trial.ev)
+        for (auto& ev : pair)
+            if (ev) cudaEventDestroy(ev);
     if (b->owns_arena && b->arena_base) cudaFree(b->arena_base);
     delete b;
 }
@@ -615,32 +869,22 @@ int fhp_batch_set_graph_steps(fhp_batch* b, int32_t steps) {
     return FHP_OK;
 }
 
-int fhp_batch_step(fhp_batch* b, int64_t n) {
-    if (!b || n < 0) return bfail(b, FHP_EINVAL, "invalid arguments");
-    DeviceGuard dg(b->device);
-    // Per-member step counts for this call.
-    int max_steps = 0;
-    const int64_t cap = n < (1 << 30) ? n : (1 << 30);
-    for (auto& m : b->members) {
-        if (!m.used) continue;
-        int64_t k = cap;
-        if (m.steps_left >= 0 && m.steps_left < k) k = m.steps_left;
-        if (m.t + k >= kMaxTime) return bfail(b, FHP_EINVAL, "a member's step counter would pass 2^48");
-        max_steps = std::max<int>(max_steps, (int)k);
-    }
-    if (max_steps == 0) return FHP_OK;
-    // Descriptors and tile list.
+namespace {
+
+// Rebuilds the tile list after membership changes (each member's tiles in
+// order, starting at its tile_base) and makes sure the device tables fit.
+int prepare_tiles(fhp_batch* b) {
     const size_t nm = b->members.size();
-    int rc = FHP_OK;
     if (b->tiles_dirty) {
         b->h_tiles.clear();
         for (size_t i = 0; i < nm; ++i) {
-            const Member& m = b->members[i];
+            Member& m = b->members[i];
             if (!m.used) continue;
+            m.tile_base = (int)b->h_tiles.size();
             const int nt = (m.g.H + m.R - 1) / m.R;
             for (int j = 0; j < nt; ++j) b->h_tiles.push_back(fhp::BatchTile{(int)i, j});
         }
-        rc = ensure_tables(b, std::max<size_t>(nm, 1), std::max<size_t>(b->h_tiles.size(), 1));
+        int rc = ensure_tables(b, std::max<size_t>(nm, 1), std::max<size_t>(b->h_tiles.size(), 1));
         if (rc != FHP_OK) return rc;
         cudaError_t e = cudaMemcpyAsync(b->d_tiles, b->h_tiles.data(), b->h_tiles.size() * sizeof(fhp::BatchTile),
                                         cudaMemcpyHostToDevice, b->stream);
@@ -648,17 +892,24 @@ int fhp_batch_step(fhp_batch* b, int64_t n) {
         b->ntiles = (int)b->h_tiles.size();
         b->tiles_dirty = false;
     }
-    rc = ensure_tables(b, std::max<size_t>(nm, 1), std::max<size_t>(b->h_tiles.size(), 1));
-    if (rc != FHP_OK) return rc;
+    return ensure_tables(b, std::max<size_t>(nm, 1), std::max<size_t>(b->h_tiles.size(), 1));
+}
+
+// Uploads the descriptors of a call of `chunk` steps (each member advances
+// min(chunk, its budget) steps); returns the largest count in *max_steps.
+int upload_descriptors(fhp_batch* b, int chunk, std::vector<int>& steps_of, int* max_steps) {
+    const size_t nm = b->members.size();
     b->h_lats.assign(nm, fhp::BatchLattice{});
-    std::vector<int> steps_of(nm, 0);
+    steps_of.assign(nm, 0);
+    *max_steps = 0;
     for (size_t i = 0; i < nm; ++i) {
         const Member& m = b->members[i];
         fhp::BatchLattice& L = b->h_lats[i];
         if (!m.used) continue;
-        int64_t k = cap;
+        int64_t k = chunk;
         if (m.steps_left >= 0 && m.steps_left < k) k = m.steps_left;
         steps_of[i] = (int)k;
+        *max_steps = std::max(*max_steps, (int)k);
         L.a.src = m.buf[m.cur];
         L.a.dst = m.buf[m.cur ^ 1];
         L.a.solid = m.solid;
@@ -682,14 +933,60 @@ int fhp_batch_step(fhp_batch* b, int64_t n) {
         L.cur = m.cur;
         L.steps = (int)k;
         L.force = m.ft.q[32] != 0;
+        L.tile_base = m.tile_base;
     }
+    if (*max_steps == 0) return FHP_OK;
     cudaError_t e = cudaMemcpyAsync(b->d_lats, b->h_lats.data(), nm * sizeof(fhp::BatchLattice),
                                     cudaMemcpyHostToDevice, b->stream);
+    if (e != cudaSuccess) return bcuda(b, e, "uploading the descriptors");
+    return FHP_OK;
+}
+
+void finish_call(fhp_batch* b, const std::vector<int>& steps_of) {
+    for (size_t i = 0; i < b->members.size(); ++i) {
+        Member& m = b->members[i];
+        if (!m.used) continue;
+        const int k = steps_of[i];
+        m.t += k;
+        m.cur ^= (k & 1);
+        if (m.steps_left >= 0) m.steps_left -= k;
+    }
+}
+
+// One cooperative launch of the multi-step kernel for `max_steps` steps.
+int launch_run_call(fhp_batch* b, int max_steps) {
+    cudaError_t e;
+    const int bps = fhp::batch_run_blocks_per_sm(b->device, &e);
+    if (e != cudaSuccess) return bcuda(b, e, "configuring the multi-step batch kernel");
+    int sms = 0;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
+    if (e != cudaSuccess) return bcuda(b, e, "querying the SM count");
+    const int grid = std::min(b->ntiles, bps * sms);
+    e = cudaMemsetAsync(b->d_done, 0, (size_t)b->ntiles * sizeof(unsigned int), b->stream);
+    if (e != cudaSuccess) return bcuda(b, e, "clearing the tile counters");
+    const fhp::BatchLattice* lats = b->d_lats;
+    const fhp::BatchTile* tiles = b->d_tiles;
+    int ntiles = b->ntiles;
+    int nsteps = max_steps;
+    unsigned int* done = b->d_done;
+    unsigned int* err = b->d_err;
+    void* args[] = {(void*)&lats, (void*)&tiles, (void*)&ntiles, (void*)&nsteps, (void*)&done, (void*)&err};
+    const size_t smem = fhp::kBPrefixBytes + fhp::kBStages * fhp::kBStageBudget;
+    e = cudaLaunchCooperativeKernel((const void*)fhp::fhp_batch_run_kernel, dim3(grid), dim3(fhp::kBRunThreads), args,
+                                    smem, b->stream);
+    if (e != cudaSuccess) return bcuda(b, e, "launching the multi-step batch kernel");
+    ++b->launches;
+    return FHP_OK;
+}
+
+// max_steps launches of the single-step kernel, replayed from a captured
+// graph in groups of graph_steps.
+int launch_step_call(fhp_batch* b, int max_steps) {
+    cudaError_t e = cudaSuccess;
     b->h_counters[0] = 0;
     b->h_counters[1] = b->ntiles;
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(b->d_step_base, b->h_counters, sizeof b->h_counters, cudaMemcpyHostToDevice, b->stream);
-    if (e != cudaSuccess) return bcuda(b, e, "uploading the descriptors");
+    e = cudaMemcpyAsync(b->d_step_base, b->h_counters, sizeof b->h_counters, cudaMemcpyHostToDevice, b->stream);
+    if (e != cudaSuccess) return bcuda(b, e, "uploading the step counters");
     int bps = fhp::batch_blocks_per_sm(b->device, &e);
     if (e != cudaSuccess) return bcuda(b, e, "configuring the batch kernel");
     int sms = 0;
@@ -701,20 +998,10 @@ int fhp_batch_step(fhp_batch* b, int64_t n) {
     const int full_grid = bps * sms;
     const int grid = std::min(b->ntiles, full_grid);
     const size_t smem = fhp::kBPrefixBytes + fhp::kBStages * fhp::kBStageBudget;
-    auto launch_steps = [&](int first, int count) -> cudaError_t {
-        for (int o = first; o < first + count; ++o) {
-            fhp::fhp_batch_kernel<<<grid, fhp::kBThreads, smem, b->stream>>>(b->d_lats, b->d_tiles,
-                                                                              b->d_step_base, o, b->d_err);
-            cudaError_t le = cudaGetLastError();
-            if (le != cudaSuccess) return le;
-        }
-        return cudaSuccess;
-    };
     int done = 0;
     const int G = b->graph_steps;
     if (G > 0 && max_steps >= G) {
         if (!b->graph) {
-            drop_graph(b);
             cudaStream_t cs;
             e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
             if (e != cudaSuccess) return bcuda(b, e, "creating the capture stream");
@@ -742,21 +1029,153 @@ int fhp_batch_step(fhp_batch* b, int64_t n) {
             done += G;
         }
     }
-    if (done < max_steps) {
-        e = launch_steps(0, max_steps - done);
+    for (int o = 0; o < max_steps - done; ++o) {
+        fhp::fhp_batch_kernel<<<grid, fhp::kBThreads, smem, b->stream>>>(b->d_lats, b->d_tiles, b->d_step_base, o,
+                                                                          b->d_err);
+        e = cudaGetLastError();
         if (e != cudaSuccess) return bcuda(b, e, "launching the batch kernel");
-        b->launches += max_steps - done;
-    }
-    for (size_t i = 0; i < nm; ++i) {
-        Member& m = b->members[i];
-        if (!m.used) continue;
-        const int k = steps_of[i];
-        m.t += k;
-        m.cur ^= (k & 1);
-        if (m.steps_left >= 0) m.steps_left -= k;
+        ++b->launches;
     }
     return FHP_OK;
 }
+
+}  // namespace
+
+namespace {
+
+// Node updates one call issues (members advance steps_of[i] steps).
+double issued_updates(const fhp_batch* b, const std::vector<int>& steps_of) {
+    double u = 0.0;
+    for (size_t i = 0; i < b->members.size(); ++i)
+        if (b->members[i].used) u += (double)b->members[i].g.W * b->members[i].g.H * steps_of[i];
+    return u;
+}
+
+// Online autotuning of the automatic batch kernel choice.  Batches are
+// classed by the binary order of magnitude of their tile count; the first
+// long enough call in a class runs half its steps with each kernel, timed by
+// events on the batch's stream, and a later call reads the events (without
+// waiting) and records the kernel with more node updates per millisecond.
+int tile_class(int ntiles) {
+    int c = 0;
+    while (ntiles > 1 && c < kTuneClasses - 1) {
+        ntiles >>= 1;
+        ++c;
+    }
+    return c;
+}
+
+void collect_trial(fhp_batch* b) {
+    TuneTrial& tr = b->trial;
+    if (tr.cls < 0) return;
+    for (int k = 0; k < 2; ++k)
+        if (cudaEventQuery(tr.ev[k][1]) != cudaSuccess) return;  // not finished yet: look again next call
+    float ms[2] = {0.0f, 0.0f};
+    bool ok = true;
+    for (int k = 0; k < 2; ++k) ok = ok && cudaEventElapsedTime(&ms[k], tr.ev[k][0], tr.ev[k][1]) == cudaSuccess;
+    if (ok && ms[0] > 0.0f && ms[1] > 0.0f) {
+        const double rate_single = tr.updates[0] / ms[0], rate_multi = tr.updates[1] / ms[1];
+        b->tuned[tr.cls] = rate_multi > rate_single ? FHP_BATCH_KERNEL_MULTI_STEP : FHP_BATCH_KERNEL_SINGLE_STEP;
+    } else {
+        b->tuned[tr.cls] = FHP_BATCH_KERNEL_SINGLE_STEP;
+    }
+    tr.cls = -1;
+}
+
+int ensure_trial_events(fhp_batch* b) {
+    for (auto& pair : b->trial.ev)
+        for (auto& ev : pair)
+            if (!ev) {
+                cudaError_t e = cudaEventCreate(&ev);
+                if (e != cudaSuccess) return bcuda(b, e, "creating the tuning events");
+            }
+    return FHP_OK;
+}
+
+// One chunk of steps with the given kernel.
+int run_chunk(fhp_batch* b, int chunk, int kind, std::vector<int>& steps_of, double* updates) {
+    int max_steps = 0;
+    int rc = upload_descriptors(b, chunk, steps_of, &max_steps);
+    if (rc != FHP_OK || max_steps == 0) return rc;
+    rc = kind == FHP_BATCH_KERNEL_MULTI_STEP && max_steps >= 2 ? launch_run_call(b, max_steps)
+                                                               : launch_step_call(b, max_steps);
+    if (rc != FHP_OK) return rc;
+    if (updates) *updates = issued_updates(b, steps_of);
+    finish_call(b, steps_of);
+    return FHP_OK;
+}
+
+}  // namespace
+
+int fhp_batch_step(fhp_batch* b, int64_t n) {
+    if (!b || n < 0) return bfail(b, FHP_EINVAL, "invalid arguments");
+    DeviceGuard dg(b->device);
+    for (auto& m : b->members) {
+        if (!m.used) continue;
+        int64_t k = n;
+        if (m.steps_left >= 0 && m.steps_left < k) k = m.steps_left;
+        if (k >= kMaxTime - m.t) return bfail(b, FHP_EINVAL, "a member's step counter would pass 2^48");
+    }
+    int rc = prepare_tiles(b);
+    if (rc != FHP_OK) return rc;
+    std::vector<int> steps_of;
+    int64_t left = n;
+    if (b->step_kernel == FHP_BATCH_KERNEL_AUTO && b->ntiles > 0) {
+        collect_trial(b);
+        const int cls = tile_class(b->ntiles);
+        if (b->tuned[cls] == FHP_BATCH_KERNEL_AUTO && b->trial.cls < 0 && n >= 2 * kTuneMinSteps) {
+            // A trial: half of the call with each kernel.
+            rc = ensure_trial_events(b);
+            if (rc != FHP_OK) return rc;
+            const int half = (int)std::min<int64_t>(n / 2, (int64_t)1 << 20);
+            const int kinds[2] = {FHP_BATCH_KERNEL_SINGLE_STEP, FHP_BATCH_KERNEL_MULTI_STEP};
+            for (int k = 0; k < 2; ++k) {
+                cudaEventRecord(b->trial.ev[k][0], b->stream);
+                b->trial.updates[k] = 0.0;
+                rc = run_chunk(b, half, kinds[k], steps_of, &b->trial.updates[k]);
+                if (rc != FHP_OK) return rc;
+                cudaError_t e = cudaEventRecord(b->trial.ev[k][1], b->stream);
+                if (e != cudaSuccess) return bcuda(b, e, "recording the tuning events");
+            }
+            b->trial.cls = cls;
+            left -= 2 * half;
+        }
+    }
+    while (left > 0) {
+        // Calls are split into chunks of at most 2^24 steps (the multi-step
+        // kernel's counters hold 8 per tile and step).
+        const int chunk = (int)std::min<int64_t>(left, (int64_t)1 << 24);
+        int kind = b->step_kernel;
+        if (kind == FHP_BATCH_KERNEL_AUTO) {
+            const int t = b->tuned[tile_class(b->ntiles)];
+            kind = t == FHP_BATCH_KERNEL_AUTO ? FHP_BATCH_KERNEL_SINGLE_STEP : t;
+        }
+        rc = run_chunk(b, chunk, kind, steps_of, nullptr);
+        if (rc != FHP_OK) return rc;
+        left -= chunk;
+    }
+    return FHP_OK;
+}
+
+int fhp_batch_get_tuned_kernel(const fhp_batch* b, int32_t ntiles) {
+    if (!b || ntiles < 1) return -1;
+    return b->tuned[tile_class(ntiles)];
+}
+
+int32_t fhp_batch_tile_count(fhp_batch* b) {
+    if (!b) return -1;
+    if (prepare_tiles(b) != FHP_OK) return -1;
+    return b->ntiles;
+}
+
+int fhp_batch_set_step_kernel(fhp_batch* b, int32_t kind) {
+    if (!b || kind < FHP_BATCH_KERNEL_AUTO || kind > FHP_BATCH_KERNEL_MULTI_STEP)
+        return bfail(b, FHP_EINVAL, "batch step kernel %d not in {0, 1, 2}", kind);
+    b->step_kernel = kind;
+    return FHP_OK;
+}
+
+int fhp_batch_get_step_kernel(const fhp_batch* b) { return b ? b->step_kernel : -1; }
 
 int fhp_batch_synchronize(fhp_batch* b) {
     if (!b) return bfail(nullptr, FHP_EINVAL, "batch is NULL");

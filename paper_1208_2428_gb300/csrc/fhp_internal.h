@@ -33,6 +33,7 @@ struct Geometry {
     int nq = 0;         // quads per row
     int Pq = 0;         // row pitch in words (multiple of 4)
     size_t plane_words = 0;  // H * Pq
+    int row_base = 0;   // lattice row of array row 0 (a strip of a larger lattice; even)
 };
 
 Geometry make_geometry(int W, int H);
@@ -50,6 +51,7 @@ struct StepArgs {
     Key2 key;
     uint32_t t_lo, t_hi;
     unsigned int* err;       // set nonzero if a bounded device-side wait gives up
+    int y_base = 0;          // added to the row index that keys the random words (strips)
     ForcingTable ft;
 };
 

@@ -1,8 +1,9 @@
 // fhp_quad.cuh -- per-quad building blocks shared by the step kernels
-// (fhp_step.cu) and the temporally blocked kernel (fhp_block.cu): 128-bit
-// plane access, the one-node shifts of the motion step, scattering plus
-// forcing of one quad (4 words = 128 nodes), and the mbarrier / bulk-copy
-// helpers (inline PTX) of the shared-memory pipelines.
+// (fhp_step.cu), the temporally blocked kernel (fhp_block.cu) and the batch
+// kernels (fhp_batch.cu): 128-bit plane access, the one-node shifts of the
+// motion step, scattering plus forcing of one quad (4 words = 128 nodes), the
+// mbarrier / bulk-copy helpers (inline PTX) of the shared-memory pipelines,
+// and the completion counters of the multi-step kernels.
 #pragma once
 
 #include "fhp_device.cuh"
@@ -50,9 +51,9 @@ template <bool SOLID, bool FORCE>
 __device__ __forceinline__ void collide_quad(const StepArgs& a, const StepVar& v, int q, int y, uint4 n0, uint4 n1,
                                              uint4 n2, uint4 n3, uint4 n4, uint4 n5, uint4 i6, uint4 sd,
                                              uint4 (&o)[7]) {
-    const uint4 chi = rng_block((uint32_t)q, (uint32_t)y, v.t_lo, v.t_hi, 0u, a.key);
+    const uint4 chi = rng_block((uint32_t)q, (uint32_t)(y + a.y_base), v.t_lo, v.t_hi, 0u, a.key);
     uint4 gate = make_uint4(0u, 0u, 0u, 0u);
-    if (FORCE) gate = rng_block((uint32_t)q, (uint32_t)y, v.t_lo, v.t_hi, 1u, a.key);
+    if (FORCE) gate = rng_block((uint32_t)q, (uint32_t)(y + a.y_base), v.t_lo, v.t_hi, 1u, a.key);
 
 #define FHP_WORD(J, C)                                                                          \
     {                                                                                           \
@@ -64,7 +65,7 @@ __device__ __forceinline__ void collide_quad(const StepArgs& a, const StepVar& v
             /* u >= Q_32 >= Q_K: none of the word's candidates is forced (common case) */       \
             if (cand != 0u && (unsigned long long)u < a.ft.q[32]) {                             \
                 const uint32_t f = forced_mask(cand, u, a.ft, [&](uint32_t d) {                 \
-                    return word_of(rng_block((uint32_t)q, (uint32_t)y, v.t_lo, v.t_hi, 1u + d,   \
+                    return word_of(rng_block((uint32_t)q, (uint32_t)(y + a.y_base), v.t_lo, v.t_hi, 1u + d,   \
                                              a.key), J);                                        \
                 });                                                                             \
                 out.m5 ^= f;                                                                    \
@@ -245,6 +246,46 @@ __device__ __forceinline__ void compute_tile(const StepArgs& a, const StepVar& v
         const int r = 2 * k + h;
         quad_from_stage<SOLID, FORCE, RAGGED>(a, v, ta, stage, r, y0 + r, q);
     }
+}
+
+// Cross-CTA completion counters of the multi-step kernels (a tile's counter
+// counts the consumer warps that finished it, summed over steps).
+__device__ __forceinline__ unsigned int ld_relaxed_gpu(const unsigned int* p) {
+    unsigned int v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Wait until the counters of tiles a, b (and c if check_c) reach `target`.
+// The loads are relaxed so that they are in flight together; one acquire
+// fence after they all pass orders the later reads of the tiles' rows.
+// Gives up (false) after kWaitLimitNs.
+__device__ __noinline__ bool wait_tiles(const unsigned int* done, int ta_, int tb, int tc, bool check_c,
+                                        unsigned int target) {
+    unsigned long long start = 0;
+    for (;;) {
+        const unsigned int va = ld_relaxed_gpu(done + ta_);
+        const unsigned int vb = ld_relaxed_gpu(done + tb);
+        const unsigned int vc = check_c ? ld_relaxed_gpu(done + tc) : target;
+        if (va >= target && vb >= target && vc >= target) {
+            asm volatile("fence.acq_rel.gpu;" ::: "memory");
+            return true;
+        }
+        const unsigned long long now = global_ns();
+        if (start == 0) start = now;
+        else if (now - start > kWaitLimitNs) return false;
+        __nanosleep(32);
+    }
+}
+
+__device__ __forceinline__ void st_release_cta_shared(unsigned int* p, unsigned int v) {
+    asm volatile("st.release.cta.shared::cta.u32 [%0], %1;" ::"r"(smem_addr(p)), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ unsigned int ld_acquire_cta_shared(const unsigned int* p) {
+    unsigned int v;
+    asm volatile("ld.acquire.cta.shared::cta.u32 %0, [%1];" : "=r"(v) : "r"(smem_addr(p)) : "memory");
+    return v;
 }
 
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {

@@ -127,44 +127,6 @@ struct RunArgs {
     unsigned long long t0;
 };
 
-__device__ __forceinline__ unsigned int ld_relaxed_gpu(const unsigned int* p) {
-    unsigned int v;
-    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-
-// Wait until the counters of tiles a, b (and c if check_c) reach `target`.
-// The loads are relaxed so that they are in flight together; one acquire
-// fence after they all pass orders the later reads of the tiles' rows.
-// Gives up (false) after kWaitLimitNs.
-__device__ __noinline__ bool wait_tiles(const unsigned int* done, int ta_, int tb, int tc, bool check_c,
-                                        unsigned int target) {
-    unsigned long long start = 0;
-    for (;;) {
-        const unsigned int va = ld_relaxed_gpu(done + ta_);
-        const unsigned int vb = ld_relaxed_gpu(done + tb);
-        const unsigned int vc = check_c ? ld_relaxed_gpu(done + tc) : target;
-        if (va >= target && vb >= target && vc >= target) {
-            asm volatile("fence.acq_rel.gpu;" ::: "memory");
-            return true;
-        }
-        const unsigned long long now = global_ns();
-        if (start == 0) start = now;
-        else if (now - start > kWaitLimitNs) return false;
-        __nanosleep(32);
-    }
-}
-
-__device__ __forceinline__ void st_release_cta_shared(unsigned int* p, unsigned int v) {
-    asm volatile("st.release.cta.shared::cta.u32 [%0], %1;" ::"r"(smem_addr(p)), "r"(v) : "memory");
-}
-
-__device__ __forceinline__ unsigned int ld_acquire_cta_shared(const unsigned int* p) {
-    unsigned int v;
-    asm volatile("ld.acquire.cta.shared::cta.u32 %0, [%1];" : "=r"(v) : "r"(smem_addr(p)) : "memory");
-    return v;
-}
-
 template <bool SOLID, bool FORCE, bool RAGGED>
 __global__ void __launch_bounds__(kRunThreads, 2) fhp_run_kernel(const StepArgs a, const TileArgs ta,
                                                                  const RunArgs ra) {
@@ -603,6 +565,7 @@ cudaError_t launch_run(const Geometry& g, uint32_t* buf0, uint32_t* buf1, const 
     a.Pq = g.Pq;
     a.rows_per_warp = a.groups_per_parity = a.warps_per_row = 1;
     a.key = key;
+    a.y_base = g.row_base;
     a.t_lo = (uint32_t)t0;
     a.t_hi = (uint32_t)(t0 >> 32);
     a.err = err;
@@ -642,6 +605,7 @@ cudaError_t launch_step(const Geometry& g, const uint32_t* src, uint32_t* dst,
     a.nq = g.nq;
     a.Pq = g.Pq;
     a.key = key;
+    a.y_base = g.row_base;
     a.t_lo = (uint32_t)t;
     a.t_hi = (uint32_t)(t >> 32);
     a.err = err;

@@ -78,7 +78,17 @@ def load(path: str | None = None):
         "fhp_kernel_launches": (i64, [vp]),
         "fhp_philox4x32_10_device": (ctypes.c_int, [vp, vp, vp, i64, vp]),
         "fhp_init_random": (ctypes.c_int, [vp, ctypes.c_double]),
+        "fhp_get_temporal_block": (ctypes.c_int, [vp]),
+        "fhp_set_row_offset": (ctypes.c_int, [vp, i32]),
+        "fhp_row_pitch_words": (i32, [vp]),
+        "fhp_get_rows_device": (ctypes.c_int, [vp, i32, i32, vp]),
+        "fhp_set_rows_device": (ctypes.c_int, [vp, i32, i32, vp]),
+        "fhp_autotune": (ctypes.c_int, [vp, i32, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
         "fhp_batch_init_random": (ctypes.c_int, [vp, i32, ctypes.c_double]),
+        "fhp_batch_set_step_kernel": (ctypes.c_int, [vp, i32]),
+        "fhp_batch_get_step_kernel": (ctypes.c_int, [vp]),
+        "fhp_batch_get_tuned_kernel": (ctypes.c_int, [vp, i32]),
+        "fhp_batch_tile_count": (i32, [vp]),
         "fhp_batch_load_obstacles": (ctypes.c_int, [vp, i32, u8p]),
         "fhp_batch_lattice_bytes": (ctypes.c_size_t, [i32, i32]),
         "fhp_batch_create": (ctypes.c_int, [ctypes.POINTER(vp), ctypes.c_size_t, vp, vp]),
@@ -243,6 +253,41 @@ class Lattice:
         """0 automatic, 1 direct register loads, 2 bulk-copy shared-memory ring."""
         self._check(self._lib.fhp_set_step_kernel(self._h, int(kind)))
 
+    # -- strips of a larger lattice ------------------------------------------------
+    def set_row_offset(self, row_base: int):
+        """Array row y is row row_base + y of a larger lattice (even row_base)."""
+        self._check(self._lib.fhp_set_row_offset(self._h, int(row_base)))
+
+    @property
+    def row_pitch_words(self) -> int:
+        return int(self._lib.fhp_row_pitch_words(self._h))
+
+    def get_rows_tensor(self, y0: int, n: int, out=None):
+        """Rows [y0, y0+n) of the 7 state planes as an int32 CUDA tensor [7, n, pitch]."""
+        torch = _torch()
+        if out is None:
+            out = torch.empty((7, int(n), self.row_pitch_words), dtype=torch.int32, device=self.device)
+        self._check(self._lib.fhp_get_rows_device(self._h, int(y0), int(n), ctypes.c_void_p(out.data_ptr())))
+        return out
+
+    def set_rows_tensor(self, y0: int, rows):
+        """Inverse of get_rows_tensor (an int32 CUDA tensor [7, n, pitch])."""
+        if rows.dim() != 3 or rows.shape[0] != 7 or rows.shape[2] != self.row_pitch_words or not rows.is_contiguous():
+            raise ValueError("rows must be a contiguous [7, n, pitch] tensor")
+        self._check(self._lib.fhp_set_rows_device(self._h, int(y0), int(rows.shape[1]),
+                                                  ctypes.c_void_p(rows.data_ptr())))
+
+    @property
+    def temporal_block(self) -> int:
+        return int(self._lib.fhp_get_temporal_block(self._h))
+
+    def autotune(self, trial_steps: int = 64) -> tuple[int, int]:
+        """Time the step configurations on this lattice and record the
+        fastest for its shape; returns (kernel, temporal block)."""
+        kern, k = ctypes.c_int32(0), ctypes.c_int32(0)
+        self._check(self._lib.fhp_autotune(self._h, int(trial_steps), ctypes.byref(kern), ctypes.byref(k)))
+        return kern.value, k.value
+
     @property
     def step_kernel(self) -> int:
         return int(self._lib.fhp_get_step_kernel(self._h))
@@ -387,6 +432,24 @@ class Batch:
 
     def step(self, n: int = 1):
         self._check(self._lib.fhp_batch_step(self._h, int(n)))
+
+    def set_step_kernel(self, kind: int):
+        """0 automatic, 1 one launch per step (CUDA graphs), 2 all steps of a
+        call in one cooperative launch."""
+        self._check(self._lib.fhp_batch_set_step_kernel(self._h, int(kind)))
+
+    @property
+    def step_kernel(self) -> int:
+        return int(self._lib.fhp_batch_get_step_kernel(self._h))
+
+    @property
+    def tile_count(self) -> int:
+        return int(self._lib.fhp_batch_tile_count(self._h))
+
+    def tuned_kernel(self, ntiles: int | None = None) -> int:
+        """Kernel the automatic choice recorded for this many tiles (0: none yet)."""
+        n = self.tile_count if ntiles is None else int(ntiles)
+        return int(self._lib.fhp_batch_get_tuned_kernel(self._h, n))
 
     def set_graph_steps(self, n: int):
         self._check(self._lib.fhp_batch_set_graph_steps(self._h, int(n)))

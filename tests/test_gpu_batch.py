@@ -38,11 +38,18 @@ def oracle_alone(oracle_mod, job, s0, t0, n):
     return out
 
 
-def test_batch_matches_oracle(pkg, oracle_mod):
+# 1: one launch per step (CUDA graphs); 2: all steps of a call in one cooperative launch
+KERNELS = [1, 2]
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_batch_matches_oracle(pkg, oracle_mod, kernel):
     jobs = small_ensemble(24, 1)
     states = [j.initial_state() for j in jobs]
     arena = sum(pkg.Batch.lattice_bytes(j.W, j.H) for j in jobs) + (64 << 20)
     with pkg.Batch(arena) as b:
+        b.set_step_kernel(kernel)
+        assert b.step_kernel == kernel
         b.set_graph_steps(8)
         slots = []
         for j, s0 in zip(jobs, states):
@@ -59,13 +66,15 @@ def test_batch_matches_oracle(pkg, oracle_mod):
             assert np.array_equal(got, want), (j.name, j.W, j.H, int((got != want).sum()))
 
 
-def test_batch_continuous_membership_and_budgets(pkg, oracle_mod):
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_batch_continuous_membership_and_budgets(pkg, oracle_mod, kernel):
     """Members join, leave and carry different step budgets; each one's
     result equals its run alone."""
     jobs = small_ensemble(12, 2)
     states = [j.initial_state() for j in jobs]
     arena = sum(pkg.Batch.lattice_bytes(j.W, j.H) for j in jobs) + (64 << 20)
     with pkg.Batch(arena) as b:
+        b.set_step_kernel(kernel)
         b.set_graph_steps(4)
         slot = {}
         steps_done = {}
@@ -126,3 +135,75 @@ def test_batch_coarse_grain_and_arena_limits(pkg, oracle_mod):
         b.remove(k)
         k2 = b.add(job.W, job.H, 1, 0.0)          # memory came back
         assert b.count == 1 and k2 == k
+
+
+def test_multi_step_kernel_edge_cases(pkg, oracle_mod):
+    """Lattices of one and two tiles (a tile is its own or its only
+    neighbour), one row of quads, single-step calls, members that stop
+    inside a call, and a batch with more tiles than resident CTAs."""
+    shapes = [(32, 2), (64, 4), (128, 8), (96, 258), (4128, 6), (2048, 64), (160, 130)]
+    jobs = []
+    for i, (W, H) in enumerate(shapes):
+        jobs.append(workloads.Lattice(f"e{i}", W, H, 0.3, 31_000 + i, 0.02 if i % 2 else 0.0, 0,
+                                      obstacle="points" if i % 3 else "none", point_frac=0.03))
+    states = [j.initial_state() for j in jobs]
+    arena = sum(pkg.Batch.lattice_bytes(j.W, j.H) for j in jobs) + (64 << 20)
+    with pkg.Batch(arena) as b:
+        b.set_step_kernel(2)
+        slots = []
+        for j, s0 in zip(jobs, states):
+            k = b.add(j.W, j.H, j.seed, j.p)
+            b.set_state(k, s0)
+            slots.append(k)
+        b.set_steps_left(slots[1], 3)
+        b.set_steps_left(slots[4], 0)
+        b.step(1)
+        b.step(9)
+        b.synchronize()
+        for i, (j, s0, k) in enumerate(zip(jobs, states, slots)):
+            n = {1: 3, 4: 0}.get(i, 10)
+            want, _ = oracle_mod.run(s0, j.seed, 0, n, j.p)
+            assert b.time(k) == n
+            assert np.array_equal(b.get_state(k), want), (j.name, j.W, j.H)
+    # many tiles: 600 lattices of 128 x 512 rows (one quad per row, 256 rows per tile)
+    big = [workloads.Lattice(f"t{i}", 128, 512, 0.25, 50_000 + i, 0.0, 0) for i in range(600)]
+    with pkg.Batch(sum(pkg.Batch.lattice_bytes(j.W, j.H) for j in big) + (64 << 20)) as b:
+        b.set_step_kernel(2)
+        slots = []
+        for j in big:
+            k = b.add(j.W, j.H, j.seed, j.p)
+            b.init_random(k, j.density)
+            slots.append(k)
+        b.step(6)
+        for idx in (0, 1, 299, 599):
+            j = big[idx]
+            s0 = oracle_mod.init_random(j.W, j.H, j.seed, j.density)
+            want, _ = oracle_mod.run(s0, j.seed, 0, 6, 0.0)
+            assert np.array_equal(b.get_state(slots[idx]), want), j.name
+
+
+def test_automatic_choice_is_tuned_online_and_exact(pkg, oracle_mod):
+    """The automatic kernel choice times both kernels on a first long call
+    (half of its steps each) and records the faster for the batch's size
+    class; members stay bit-exact throughout."""
+    jobs = small_ensemble(10, 5)
+    states = [j.initial_state() for j in jobs]
+    arena = sum(pkg.Batch.lattice_bytes(j.W, j.H) for j in jobs) + (64 << 20)
+    with pkg.Batch(arena) as b:
+        assert b.step_kernel == 0
+        slots = []
+        for j, s0 in zip(jobs, states):
+            k = b.add(j.W, j.H, j.seed, j.p)
+            b.set_state(k, s0)
+            slots.append(k)
+        assert b.tuned_kernel() == 0
+        b.step(40)                 # a trial: 20 steps with each kernel
+        b.synchronize()
+        b.step(3)                  # reads the trial's events
+        assert b.tuned_kernel() in (1, 2)
+        b.step(21)
+        b.synchronize()
+        for j, s0, k in zip(jobs, states, slots):
+            want, _ = oracle_mod.run(s0, j.seed, 0, 64, j.p)
+            assert b.time(k) == 64
+            assert np.array_equal(b.get_state(k), want), j.name
