@@ -220,9 +220,9 @@ def batched_vs_per_lattice(dev, stream, count: int, steps: int, per_steps: int, 
         for j, s0 in zip(jobs, states):
             k = b.add(j.W, j.H, j.seed, j.p)
             b.set_state(k, s0)
-        b.step(64)
+        b.step(128)  # warm-up; the automatic choice times both batch kernels here (64 steps each)
         b.synchronize()
-        b.step(1)   # reads the automatic choice's first measurement (made by the warm-up call)
+        b.step(1)   # reads that measurement
         b.synchronize()
         tuned = b.tuned_kernel()
         best = None

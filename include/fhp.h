@@ -303,8 +303,9 @@ FHP_API int fhp_batch_step(fhp_batch* batch, int64_t n);
  * and its two neighbours in its lattice) are finished, tracked by per-tile
  * counters.  AUTO (default): autotuned online -- batches are classed by the
  * binary order of magnitude of their tile count (fhp_batch_tile_count); the
- * first call of at least 32 steps in a class runs half of its steps with each
- * kernel, timed with CUDA events on the batch's stream, and a later call
+ * first call in a class of at least 2 * max(16, graph steps) steps runs half
+ * of its steps with each kernel, timed with CUDA events on the batch's
+ * stream, and a later call
  * records the kernel with more node updates per millisecond for the class
  * (read without waiting); until then SINGLE_STEP runs.  Results are
  * identical for every choice. */

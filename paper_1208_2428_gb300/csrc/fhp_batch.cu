@@ -1123,7 +1123,10 @@ int fhp_batch_step(fhp_batch* b, int64_t n) {
     if (b->step_kernel == FHP_BATCH_KERNEL_AUTO && b->ntiles > 0) {
         collect_trial(b);
         const int cls = tile_class(b->ntiles);
-        if (b->tuned[cls] == FHP_BATCH_KERNEL_AUTO && b->trial.cls < 0 && n >= 2 * kTuneMinSteps) {
+        // A trial needs halves long enough for the single-step kernel to run
+        // as it normally does (from the captured graph).
+        const int64_t min_half = std::max<int64_t>(kTuneMinSteps, b->graph_steps);
+        if (b->tuned[cls] == FHP_BATCH_KERNEL_AUTO && b->trial.cls < 0 && n >= 2 * min_half) {
             // A trial: half of the call with each kernel.
             rc = ensure_trial_events(b);
             if (rc != FHP_OK) return rc;

@@ -197,13 +197,49 @@ def test_automatic_choice_is_tuned_online_and_exact(pkg, oracle_mod):
             b.set_state(k, s0)
             slots.append(k)
         assert b.tuned_kernel() == 0
+        b.set_graph_steps(8)
+        b.step(14)                 # too short for a trial (halves below 16 steps)
+        b.synchronize()
+        b.step(1)
+        assert b.tuned_kernel() == 0
         b.step(40)                 # a trial: 20 steps with each kernel
         b.synchronize()
         b.step(3)                  # reads the trial's events
         assert b.tuned_kernel() in (1, 2)
-        b.step(21)
+        b.step(6)
         b.synchronize()
         for j, s0, k in zip(jobs, states, slots):
             want, _ = oracle_mod.run(s0, j.seed, 0, 64, j.p)
             assert b.time(k) == 64
             assert np.array_equal(b.get_state(k), want), j.name
+
+
+def test_ensemble_512_in_the_benchmark_configuration(pkg, oracle_mod):
+    """The 512-lattice ensemble (sides 128..2048, 1 % point obstacles) as the
+    benchmark runs it (graphs of 64 launches, automatic kernel choice):
+    every member equals its oracle run after 6 steps, and the six smallest
+    members equal theirs after the benchmark's 2,000 steps."""
+    jobs = workloads.ensemble_512(512)
+    arena = sum(pkg.Batch.lattice_bytes(j.W, j.H) for j in jobs) + (256 << 20)
+    smallest = sorted(range(len(jobs)), key=lambda i: jobs[i].nodes)[:6]
+    with pkg.Batch(arena) as b:
+        b.set_graph_steps(64)
+        slots, states = [], []
+        for j in jobs:
+            s0 = j.initial_state()
+            k = b.add(j.W, j.H, j.seed, j.p)
+            b.set_state(k, s0)
+            slots.append(k)
+            states.append(s0)
+        b.step(6)
+        for i, (j, k) in enumerate(zip(jobs, slots)):
+            want, _ = oracle_mod.run(states[i], j.seed, 0, 6, j.p)
+            assert np.array_equal(b.get_state(k), want), j.name
+        b.step(128)              # warm-up as in the benchmark: the automatic choice measures both kernels
+        b.synchronize()
+        b.step(1994 - 128)
+        for i in smallest:
+            j = jobs[i]
+            want, _ = oracle_mod.run(states[i], j.seed, 0, 2000, j.p)
+            assert b.time(slots[i]) == 2000
+            assert np.array_equal(b.get_state(slots[i]), want), (j.name, j.W, j.H)

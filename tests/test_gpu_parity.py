@@ -160,6 +160,18 @@ def test_temporal_block_full_size_all_k(fhp_mod, oracle_mod):
         assert_same(gpu_run(fhp_mod, s0, job.seed, 0, 24, job.p, k_block=k), want, f"k={k}")
 
 
+def test_cylinder_1000_steps_same_for_every_k(fhp_mod):
+    """16384 x 4096 cylinder, the benchmark's 1,000 steps: the final state is
+    the same for k = 1, 2, 4, 8 and for the single-step ring (the oracle pins
+    the first 24 steps above; here the kernels must agree over the full run)."""
+    job = workloads.cylinder_16384x4096()
+    s0 = job.initial_state()
+    ref = gpu_run(fhp_mod, s0, job.seed, 0, job.steps, job.p)
+    for k in (2, 4, 8):
+        assert_same(gpu_run(fhp_mod, s0, job.seed, 0, job.steps, job.p, k_block=k), ref, f"1000 steps, k={k}")
+    assert_same(gpu_run(fhp_mod, s0, job.seed, 0, job.steps, job.p, kernel=2), ref, "1000 steps, ring")
+
+
 def test_parity_large_step_counter(fhp_mod, oracle_mod):
     """Counters above 2^32 use the high half of t in the random streams."""
     W, H = 256, 16
