@@ -160,6 +160,18 @@ FHP_API int fhp_set_forcing(fhp_lattice* lattice, double p);
  * Results are identical for every value.  Default 1. */
 FHP_API int fhp_set_temporal_block(fhp_lattice* lattice, int32_t k);
 
+/* Collision rule set (the paper's Fig. 2 is not legible; the default is
+ * FHP-II).  FHP_RULES_FHP_II: two-body head-on collisions turned by +-60
+ * degrees by the node's chirality bit, symmetric three-body collisions, and
+ * rest-particle creation / annihilation (rest + c_i <-> c_{i-1} + c_{i+1}).
+ * FHP_RULES_FHP_I: the original model without the rest-particle rules (a rest
+ * particle, if present, is a spectator that never changes).  Takes effect
+ * from the next step.  FHP_EINVAL for other values. */
+#define FHP_RULES_FHP_I 1
+#define FHP_RULES_FHP_II 2
+FHP_API int fhp_set_rules(fhp_lattice* lattice, int32_t rules);
+FHP_API int fhp_get_rules(const fhp_lattice* lattice);
+
 /* Row-strip decomposition of one lattice across devices (the paper's
  * multi-GPU runs, Table 1).  A strip is a lattice of its own whose array row
  * y is row row_base + y of the whole lattice: the row keys the random words,
@@ -275,6 +287,8 @@ FHP_API int fhp_batch_remove(fhp_batch* batch, int32_t slot);
 
 /* Generated initial state of a member (as fhp_init_random). */
 FHP_API int fhp_batch_init_random(fhp_batch* batch, int32_t slot, double density);
+/* Collision rule set of a member (as fhp_set_rules). */
+FHP_API int fhp_batch_set_rules(fhp_batch* batch, int32_t slot, int32_t rules);
 /* Obstacles of a member (as fhp_load_obstacles), H x W bytes, nonzero =
  * solid.  Asynchronous: the mask is copied on the batch's stream; a pageable
  * buffer may be reused on return, a page-locked one only after

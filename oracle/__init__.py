@@ -61,6 +61,11 @@ def _load():
         lib.oracle_rng_word.restype = ctypes.c_uint32
         lib.oracle_build_table.argtypes = [ctypes.c_int, u8p]
         lib.oracle_build_table.restype = None
+        lib.oracle_build_table_rules.argtypes = [ctypes.c_int, ctypes.c_int, u8p]
+        lib.oracle_build_table_rules.restype = None
+        lib.oracle_run_rules.argtypes = [ctypes.c_int, ctypes.c_int, u8p, u8p, ctypes.c_uint64,
+                                         ctypes.c_uint64, ctypes.c_int64, ctypes.c_double, ctypes.c_int]
+        lib.oracle_run_rules.restype = ctypes.c_int64
         lib.oracle_neighbour.argtypes = [ctypes.c_int] * 5 + [ip, ip]
         lib.oracle_neighbour.restype = None
         lib.oracle_forcing_thresholds.argtypes = [ctypes.c_double, u64p]
@@ -104,10 +109,14 @@ def rng_word(seed: int, t: int, y: int, w: int, stream: int) -> int:
     return int(_load().oracle_rng_word(seed, t, y, w, stream))
 
 
-def table(chirality: int) -> np.ndarray:
-    """The 256-entry scattering table for chirality 0 or 1 (uint8[256])."""
+def table(chirality: int, rules: int = 2) -> np.ndarray:
+    """The 256-entry scattering table for chirality 0 or 1 (uint8[256]) of
+    rule set 2 (FHP-II) or 1 (FHP-I)."""
     out = np.zeros(256, dtype=np.uint8)
-    _load().oracle_build_table(int(chirality), _ptr(out, ctypes.c_uint8))
+    if rules == 2:
+        _load().oracle_build_table(int(chirality), _ptr(out, ctypes.c_uint8))
+    else:
+        _load().oracle_build_table_rules(int(rules), int(chirality), _ptr(out, ctypes.c_uint8))
     return out
 
 
@@ -124,8 +133,9 @@ def forcing_thresholds(p: float) -> np.ndarray:
     return q
 
 
-def run(state: np.ndarray, seed: int, t0: int, n: int, p: float = 0.0) -> tuple[np.ndarray, int]:
-    """Advance an H x W uint8 lattice by n steps from step t0.
+def run(state: np.ndarray, seed: int, t0: int, n: int, p: float = 0.0, rules: int = 2) -> tuple[np.ndarray, int]:
+    """Advance an H x W uint8 lattice by n steps from step t0 (rule set 2 =
+    FHP-II, 1 = FHP-I).
 
     Returns (new state, number of forcing events)."""
     s = np.array(state, dtype=np.uint8, order="C", copy=True)
@@ -135,8 +145,14 @@ def run(state: np.ndarray, seed: int, t0: int, n: int, p: float = 0.0) -> tuple[
     if W % 32 or W < 32 or H % 2 or H < 2:
         raise ValueError("W must be a positive multiple of 32 and H even")
     scratch = np.empty_like(s)
-    ev = _load().oracle_run(W, H, _ptr(s, ctypes.c_uint8), _ptr(scratch, ctypes.c_uint8),
-                            int(seed), int(t0), int(n), float(p))
+    if rules == 2:
+        ev = _load().oracle_run(W, H, _ptr(s, ctypes.c_uint8), _ptr(scratch, ctypes.c_uint8),
+                                int(seed), int(t0), int(n), float(p))
+    else:
+        ev = _load().oracle_run_rules(W, H, _ptr(s, ctypes.c_uint8), _ptr(scratch, ctypes.c_uint8),
+                                      int(seed), int(t0), int(n), float(p), int(rules))
+        if ev < 0:
+            raise ValueError("rules must be 1 or 2")
     return s, int(ev)
 
 

@@ -105,7 +105,10 @@ ORACLE_EXPORT uint32_t oracle_rng_word(uint64_t seed, uint64_t t, int y, int w, 
 
 static int dir_bit(int i) { return 1 << (((i % 6) + 6) % 6); }
 
-ORACLE_EXPORT void oracle_build_table(int chirality, uint8_t table[256]) {
+/* Rule sets: 2 = FHP-II (reading R-rules), 1 = FHP-I (the original model of
+ * Frisch, Hasslacher and Pomeau: head-on and symmetric three-body collisions
+ * only; a rest particle, if present, is a spectator that never changes). */
+ORACLE_EXPORT void oracle_build_table_rules(int rules, int chirality, uint8_t table[256]) {
     for (int b = 0; b < 256; ++b) {
         int moving = b & 0x3F;
         int rest = (b >> REST_BIT) & 1;
@@ -137,9 +140,10 @@ ORACLE_EXPORT void oracle_build_table(int chirality, uint8_t table[256]) {
                 if (moving == even) { out = (b & 0xC0) | odd; done = 1; }
                 else if (moving == odd) { out = (b & 0xC0) | even; done = 1; }
             }
-            /* Rest-particle collisions: a rest particle plus one moving
-             * particle i become two moving particles i-1 and i+1, and back. */
-            for (int i = 0; i < 6 && !done; ++i) {
+            /* Rest-particle collisions (FHP-II only): a rest particle plus
+             * one moving particle i become two moving particles i-1 and i+1,
+             * and back. */
+            for (int i = 0; i < 6 && !done && rules == 2; ++i) {
                 int pair = dir_bit(i - 1) | dir_bit(i + 1);
                 if (rest && moving == dir_bit(i)) {
                     out = pair;                       /* rest bit cleared */
@@ -152,6 +156,10 @@ ORACLE_EXPORT void oracle_build_table(int chirality, uint8_t table[256]) {
         }
         table[b] = (uint8_t)out;
     }
+}
+
+ORACLE_EXPORT void oracle_build_table(int chirality, uint8_t table[256]) {
+    oracle_build_table_rules(2, chirality, table);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -277,13 +285,20 @@ static int64_t step_once(int W, int H, const uint8_t* in, uint8_t* out, uint64_t
 }
 
 static int64_t run_rows(int W, int H, uint8_t* state, uint8_t* scratch, uint64_t seed, uint64_t t0, int64_t n,
-                        double p, int64_t row_base, int Hg);
+                        double p, int64_t row_base, int Hg, int rules);
 
 /* Advance `state` (H x W bytes) by n steps starting at step t0.  `scratch`
  * must hold H x W bytes.  Returns the total number of forcing events. */
 ORACLE_EXPORT int64_t oracle_run(int W, int H, uint8_t* state, uint8_t* scratch, uint64_t seed,
                                  uint64_t t0, int64_t n, double p) {
-    return run_rows(W, H, state, scratch, seed, t0, n, p, 0, H);
+    return run_rows(W, H, state, scratch, seed, t0, n, p, 0, H, 2);
+}
+
+/* oracle_run with the rule set chosen (1 = FHP-I, 2 = FHP-II). */
+ORACLE_EXPORT int64_t oracle_run_rules(int W, int H, uint8_t* state, uint8_t* scratch, uint64_t seed, uint64_t t0,
+                                       int64_t n, double p, int rules) {
+    if (rules != 1 && rules != 2) return -1;
+    return run_rows(W, H, state, scratch, seed, t0, n, p, 0, H, rules);
 }
 
 /* A strip of a larger lattice, for the row-strip decomposition across
@@ -296,14 +311,14 @@ ORACLE_EXPORT int64_t oracle_run(int W, int H, uint8_t* state, uint8_t* scratch,
 ORACLE_EXPORT int64_t oracle_run_rows(int W, int H, uint8_t* state, uint8_t* scratch, uint64_t seed, uint64_t t0,
                                       int64_t n, double p, int64_t row_base, int Hg) {
     if ((row_base & 1) || (H & 1) || Hg < 2) return -1;
-    return run_rows(W, H, state, scratch, seed, t0, n, p, row_base, Hg);
+    return run_rows(W, H, state, scratch, seed, t0, n, p, row_base, Hg, 2);
 }
 
 static int64_t run_rows(int W, int H, uint8_t* state, uint8_t* scratch, uint64_t seed, uint64_t t0, int64_t n,
-                        double p, int64_t row_base, int Hg) {
+                        double p, int64_t row_base, int Hg, int rules) {
     uint8_t table[2][256];
-    oracle_build_table(0, table[0]);
-    oracle_build_table(1, table[1]);
+    oracle_build_table_rules(rules, 0, table[0]);
+    oracle_build_table_rules(rules, 1, table[1]);
     uint64_t q[33];
     oracle_forcing_thresholds(p, q);
     int force_on = q[32] != 0;

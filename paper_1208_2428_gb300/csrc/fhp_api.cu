@@ -479,6 +479,16 @@ int fhp_get_step_kernel(const fhp_lattice* h) {
     return fhp::resolved_step_kernel(h->g, h->has_solid, kernel);
 }
 
+int fhp_set_rules(fhp_lattice* h, int32_t rules) {
+    if (!h) return fail(nullptr, FHP_EINVAL, "lattice is NULL");
+    if (rules != FHP_RULES_FHP_I && rules != FHP_RULES_FHP_II)
+        return fail(h, FHP_EINVAL, "rule set %d is not FHP_RULES_FHP_I (1) or FHP_RULES_FHP_II (2)", rules);
+    h->g.rules = rules;
+    return FHP_OK;
+}
+
+int fhp_get_rules(const fhp_lattice* h) { return h ? h->g.rules : -1; }
+
 int fhp_set_row_offset(fhp_lattice* h, int32_t row_base) {
     if (!h) return fail(nullptr, FHP_EINVAL, "lattice is NULL");
     if (row_base % 2) return fail(h, FHP_EINVAL, "row offset %d must be even", row_base);

@@ -789,6 +789,14 @@ int fhp_batch_load_obstacles(fhp_batch* b, int32_t slot, const uint8_t* host_mas
     return FHP_OK;
 }
 
+int fhp_batch_set_rules(fhp_batch* b, int32_t slot, int32_t rules) {
+    Member* m = member(b, slot);
+    if (!m || (rules != FHP_RULES_FHP_I && rules != FHP_RULES_FHP_II))
+        return bfail(b, FHP_EINVAL, "invalid slot %d or rule set %d", slot, rules);
+    m->g.rules = rules;
+    return FHP_OK;
+}
+
 int fhp_batch_get_state(fhp_batch* b, int32_t slot, uint8_t* host_bytes) {
     Member* m = member(b, slot);
     if (!m || !host_bytes) return bfail(b, FHP_EINVAL, "invalid slot %d or NULL bytes", slot);
@@ -920,6 +928,7 @@ int upload_descriptors(fhp_batch* b, int chunk, std::vector<int>& steps_of, int*
         L.a.Pq = m.g.Pq;
         L.a.rows_per_warp = L.a.groups_per_parity = L.a.warps_per_row = 1;
         L.a.key = fhp::Key2{(uint32_t)m.seed, (uint32_t)(m.seed >> 32)};
+        L.a.rest_rules = fhp::rest_rules_mask(m.g);
         L.a.t_lo = (uint32_t)m.t;
         L.a.t_hi = (uint32_t)(m.t >> 32);
         L.a.err = b->d_err;

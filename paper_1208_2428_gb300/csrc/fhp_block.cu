@@ -246,6 +246,7 @@ cudaError_t launch_block(const Geometry& g, const uint32_t* src, uint32_t* dst, 
     a.rows_per_warp = a.groups_per_parity = a.warps_per_row = 1;
     a.key = key;
     a.y_base = g.row_base;
+    a.rest_rules = rest_rules_mask(g);
     a.t_lo = (uint32_t)t0;
     a.t_hi = (uint32_t)(t0 >> 32);
     a.err = err;

@@ -46,7 +46,8 @@ __device__ __forceinline__ uint32_t word_of(const uint4& v, int j) {
 }
 
 // ---------------------------------------------------------------------------
-// Scattering of 32 nodes at once (FHP-II rule set, bounce-back on solid).
+// Scattering of 32 nodes at once (FHP-II rule set, or FHP-I when the
+// rest-particle rules are masked off, bounce-back on solid).
 // Every rule of the set exchanges the particles of a node for another set
 // with the same mass and momentum, so the update is a per-bit flip mask:
 //   head-on pair {i, i+3} (others empty)  -> turned by +60 deg (chi 0) or -60 deg (chi 1)
@@ -59,7 +60,10 @@ struct Planes7 {
     uint32_t m0, m1, m2, m3, m4, m5, rest;
 };
 
-__host__ __device__ __forceinline__ Planes7 scatter(const Planes7 in, uint32_t solid, uint32_t chi) {
+// rest_rules: all ones applies the rest-particle rules (FHP-II), zero skips
+// them (FHP-I: head-on and three-body collisions only).
+__host__ __device__ __forceinline__ Planes7 scatter(const Planes7 in, uint32_t solid, uint32_t chi,
+                                                    uint32_t rest_rules = 0xFFFFFFFFu) {
     const uint32_t a0 = in.m0, a1 = in.m1, a2 = in.m2, a3 = in.m3, a4 = in.m4, a5 = in.m5;
     const uint32_t r = in.rest;
 
@@ -86,9 +90,9 @@ __host__ __device__ __forceinline__ Planes7 scatter(const Planes7 in, uint32_t s
     const uint32_t two0 = lone5 & lone1 & empty0, two3 = lone2 & lone4 & empty0;
     const uint32_t two1 = lone0 & lone2 & empty1, two4 = lone3 & lone5 & empty1;
     const uint32_t two2 = lone1 & lone3 & empty2, two5 = lone4 & lone0 & empty2;
-    const uint32_t q0 = (r & one0) | (~r & two0), q1 = (r & one1) | (~r & two1);
-    const uint32_t q2 = (r & one2) | (~r & two2), q3 = (r & one3) | (~r & two3);
-    const uint32_t q4 = (r & one4) | (~r & two4), q5 = (r & one5) | (~r & two5);
+    const uint32_t q0 = ((r & one0) | (~r & two0)) & rest_rules, q1 = ((r & one1) | (~r & two1)) & rest_rules;
+    const uint32_t q2 = ((r & one2) | (~r & two2)) & rest_rules, q3 = ((r & one3) | (~r & two3)) & rest_rules;
+    const uint32_t q4 = ((r & one4) | (~r & two4)) & rest_rules, q5 = ((r & one5) | (~r & two5)) & rest_rules;
 
     // Head-on flips of movers j and j+3: pair j%3 itself, and the pair it is
     // turned onto, which depends on the chirality.

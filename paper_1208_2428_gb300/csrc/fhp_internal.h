@@ -34,7 +34,11 @@ struct Geometry {
     int Pq = 0;         // row pitch in words (multiple of 4)
     size_t plane_words = 0;  // H * Pq
     int row_base = 0;   // lattice row of array row 0 (a strip of a larger lattice; even)
+    int rules = 2;      // collision rule set: 2 = FHP-II, 1 = FHP-I
 };
+
+// Mask that enables the rest-particle rules of the bit-sliced scattering.
+inline uint32_t rest_rules_mask(const Geometry& g) { return g.rules == 1 ? 0u : 0xFFFFFFFFu; }
 
 Geometry make_geometry(int W, int H);
 
@@ -52,6 +56,7 @@ struct StepArgs {
     uint32_t t_lo, t_hi;
     unsigned int* err;       // set nonzero if a bounded device-side wait gives up
     int y_base = 0;          // added to the row index that keys the random words (strips)
+    uint32_t rest_rules = 0xFFFFFFFFu;  // ones: FHP-II rest-particle rules on; zero: FHP-I
     ForcingTable ft;
 };
 

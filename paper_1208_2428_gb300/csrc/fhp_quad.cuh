@@ -58,7 +58,7 @@ __device__ __forceinline__ void collide_quad(const StepArgs& a, const StepVar& v
 #define FHP_WORD(J, C)                                                                          \
     {                                                                                           \
         Planes7 in{n0.C, n1.C, n2.C, n3.C, n4.C, n5.C, i6.C};                                   \
-        Planes7 out = scatter(in, SOLID ? sd.C : 0u, chi.C);                                    \
+        Planes7 out = scatter(in, SOLID ? sd.C : 0u, chi.C, a.rest_rules);                      \
         if (FORCE) {                                                                            \
             const uint32_t cand = (SOLID ? ~sd.C : 0xFFFFFFFFu) & out.m5 & ~out.m2;             \
             const uint32_t u = gate.C;                                                          \

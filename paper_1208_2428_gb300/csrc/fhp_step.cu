@@ -566,6 +566,7 @@ cudaError_t launch_run(const Geometry& g, uint32_t* buf0, uint32_t* buf1, const 
     a.rows_per_warp = a.groups_per_parity = a.warps_per_row = 1;
     a.key = key;
     a.y_base = g.row_base;
+    a.rest_rules = rest_rules_mask(g);
     a.t_lo = (uint32_t)t0;
     a.t_hi = (uint32_t)(t0 >> 32);
     a.err = err;
@@ -606,6 +607,7 @@ cudaError_t launch_step(const Geometry& g, const uint32_t* src, uint32_t* dst,
     a.Pq = g.Pq;
     a.key = key;
     a.y_base = g.row_base;
+    a.rest_rules = rest_rules_mask(g);
     a.t_lo = (uint32_t)t;
     a.t_hi = (uint32_t)(t >> 32);
     a.err = err;

@@ -80,6 +80,9 @@ def load(path: str | None = None):
         "fhp_init_random": (ctypes.c_int, [vp, ctypes.c_double]),
         "fhp_get_temporal_block": (ctypes.c_int, [vp]),
         "fhp_set_row_offset": (ctypes.c_int, [vp, i32]),
+        "fhp_set_rules": (ctypes.c_int, [vp, i32]),
+        "fhp_get_rules": (ctypes.c_int, [vp]),
+        "fhp_batch_set_rules": (ctypes.c_int, [vp, i32, i32]),
         "fhp_row_pitch_words": (i32, [vp]),
         "fhp_get_rows_device": (ctypes.c_int, [vp, i32, i32, vp]),
         "fhp_set_rows_device": (ctypes.c_int, [vp, i32, i32, vp]),
@@ -253,6 +256,15 @@ class Lattice:
         """0 automatic, 1 direct register loads, 2 bulk-copy shared-memory ring."""
         self._check(self._lib.fhp_set_step_kernel(self._h, int(kind)))
 
+    # -- collision rules -------------------------------------------------------------
+    def set_rules(self, rules: int):
+        """2: FHP-II (default); 1: FHP-I (no rest-particle collisions)."""
+        self._check(self._lib.fhp_set_rules(self._h, int(rules)))
+
+    @property
+    def rules(self) -> int:
+        return int(self._lib.fhp_get_rules(self._h))
+
     # -- strips of a larger lattice ------------------------------------------------
     def set_row_offset(self, row_base: int):
         """Array row y is row row_base + y of a larger lattice (even row_base)."""
@@ -406,6 +418,9 @@ class Batch:
 
     def init_random(self, slot: int, density: float):
         self._check(self._lib.fhp_batch_init_random(self._h, int(slot), float(density)))
+
+    def set_rules(self, slot: int, rules: int):
+        self._check(self._lib.fhp_batch_set_rules(self._h, int(slot), int(rules)))
 
     def load_obstacles(self, slot: int, mask: np.ndarray):
         m = np.ascontiguousarray(mask).astype(np.uint8, copy=False)

@@ -59,7 +59,8 @@ def momentum(dirs) -> tuple[float, float]:
     return (sum(VEL[i][0] for i in dirs), sum(VEL[i][1] for i in dirs))
 
 
-def scatter(byte: int, chirality: int) -> int:
+def scatter(byte: int, chirality: int, rules: int = 2) -> int:
+    """rules 2: FHP-II; rules 1: FHP-I (no rest-particle collisions)."""
     solid = bool(byte & 0x80)
     rest = bool(byte & 0x40)
     dirs = [i for i in range(6) if byte >> i & 1]
@@ -76,6 +77,8 @@ def scatter(byte: int, chirality: int) -> int:
         new = [rotate(i, turn) for i in dirs]
     elif len(dirs) == 3 and zero and all(rotate(i, 3) not in dirs for i in dirs):
         new = [rotate(i, 1) for i in dirs]
+    elif rules == 1:
+        pass
     elif rest and len(dirs) == 1:
         i = dirs[0]
         new = [rotate(i, 1), rotate(i, -1)]

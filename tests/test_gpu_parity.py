@@ -316,3 +316,46 @@ def test_device_philox_matches_oracle(fhp_mod, oracle_mod):
     got = out.cpu().numpy().view(np.uint32)
     for i in list(range(0, n, 997)) + [n - 1]:
         assert np.array_equal(got[i], oracle_mod.philox4x32_10(ctr[i], key[i])), i
+
+
+@pytest.mark.parametrize("kernel,k", [(1, 1), (2, 1), (3, 1), (0, 2), (0, 4)])
+def test_fhp1_rules_parity(fhp_mod, oracle_mod, kernel, k):
+    """FHP-I (no rest-particle collisions) on every kernel, with walls,
+    points and forcing, against the oracle's FHP-I run."""
+    W, H, seed, p = 1024, 130, 4321, 0.01
+    job = workloads.Lattice("fhp1", W, H, 0.3, seed, p, 0, obstacle="points", point_frac=0.02)
+    s0 = job.initial_state()
+    want, _ = oracle_mod.run(s0, seed, 2, 17, p, rules=1)
+    with fhp_mod.Lattice(W, H, seed=seed, forcing_p=p, step_kernel=kernel) as lat:
+        lat.set_rules(1)
+        assert lat.rules == 1
+        lat.set_temporal_block(k)
+        lat.set_state(s0)
+        lat.set_time(2)
+        lat.step(17)
+        got = lat.get_state()
+    assert_same(got, want, f"FHP-I kernel {kernel} k {k}")
+    # rest particles are spectators under FHP-I
+    assert int(np.count_nonzero(got & 0x40)) == int(np.count_nonzero(s0 & 0x40))
+    # and FHP-II gives a different result on the same input
+    other, _ = oracle_mod.run(s0, seed, 2, 17, p, rules=2)
+    assert not np.array_equal(other, want)
+
+
+def test_fhp1_batch_member(fhp_mod, oracle_mod):
+    W, H = 512, 64
+    jobs = [workloads.Lattice(f"r{r}", W, H, 0.3, 70 + r, 0.0, 0) for r in (1, 2)]
+    with fhp_mod.Batch(2 * fhp_mod.Batch.lattice_bytes(W, H) + (16 << 20)) as b:
+        slots = []
+        for r, j in zip((1, 2), jobs):
+            k = b.add(W, H, j.seed, 0.0)
+            b.set_rules(k, r)
+            b.set_state(k, j.initial_state())
+            slots.append(k)
+        b.step(9)
+        for r, j, k in zip((1, 2), jobs, slots):
+            want, _ = oracle_mod.run(j.initial_state(), j.seed, 0, 9, 0.0, rules=r)
+            assert np.array_equal(b.get_state(k), want), r
+    with fhp_mod.Lattice(W, H) as lat:
+        with pytest.raises(fhp_mod.FhpError):
+            lat.set_rules(3)

@@ -522,3 +522,47 @@ def test_init_random_closed_forms_and_statistics(oracle_mod):
     u = (word >> 16) if i % 2 else (word & 0xFFFF)
     s2 = oracle_mod.init_random(W, H, seed, 0.5)
     assert (int(s2[y, x]) >> b & 1) == (1 if u < 32768 else 0)
+
+
+# ---------------------------------------------------------------------------
+# FHP-I rule set (head-on and three-body collisions only; the rest particle,
+# if any, is a spectator).
+# ---------------------------------------------------------------------------
+def test_fhp1_table_against_geometric_rules_and_invariants(oracle_mod):
+    for chi in (0, 1):
+        t1 = oracle_mod.table(chi, rules=1)
+        t2 = oracle_mod.table(chi, rules=2)
+        for b in range(256):
+            out = int(t1[b])
+            assert out == naive.scatter(b, chi, rules=1), (chi, bin(b))
+            assert (out ^ b) & 0xC0 == 0                       # rest bit and solid flag never change
+            assert bin(out).count("1") == bin(b).count("1")    # mass
+            if not b & 0x80:
+                assert naive.momentum([i for i in range(6) if out >> i & 1]) == pytest.approx(
+                    naive.momentum([i for i in range(6) if b >> i & 1]), abs=1e-9)
+        # differs from FHP-II exactly on the twelve rest-particle patterns
+        diff = [b for b in range(256) if t1[b] != t2[b]]
+        assert len(diff) == 12 and all(b & 0x80 == 0 for b in diff)
+        assert sorted(diff) == sorted([0x40 | (1 << i) for i in range(6)]
+                                      + [(1 << ((i + 5) % 6)) | (1 << ((i + 1) % 6)) for i in range(6)])
+    # the two chiralities are inverse permutations
+    t0, t1_ = oracle_mod.table(0, rules=1), oracle_mod.table(1, rules=1)
+    assert all(int(t1_[int(t0[b])]) == b for b in range(256))
+
+
+@pytest.mark.parametrize("W,H,p", [(32, 4, 0.0), (64, 6, 0.2)])
+def test_fhp1_brute_force_naive_model(oracle_mod, W, H, p):
+    rng = np.random.Generator(np.random.PCG64(17))
+    s = rng.integers(0, 128, size=(H, W), dtype=np.uint8)
+    s[0, :5] |= 0x80
+    seed, cur = 5, s.copy()
+    orig_scatter = naive.scatter
+    try:
+        naive.scatter = lambda b, c, rules=1: orig_scatter(b, c, rules=1)
+        for t in range(4):
+            cur = naive.step(cur, seed, t, p, oracle_mod.rng_word)
+    finally:
+        naive.scatter = orig_scatter
+    got, _ = oracle_mod.run(s, seed, 0, 4, p, rules=1)
+    assert np.array_equal(got, cur)
+    assert int(np.count_nonzero(got & 0x40)) == int(np.count_nonzero(s & 0x40))  # rest particles never move or change

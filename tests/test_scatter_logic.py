@@ -21,13 +21,15 @@ def host_scatter(tmp_path_factory):
     subprocess.run([nvcc, "-shared", "-Xcompiler", "-fPIC", "-std=c++17", "-o", str(out),
                     os.path.join(HERE, "csrc", "host_scatter.cu")], check=True)
     lib = ctypes.CDLL(str(out))
-    lib.host_scatter_words.argtypes = [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_void_p]
+    lib.host_scatter_words.argtypes = [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
+                                       ctypes.c_void_p]
     lib.host_scatter_words.restype = None
     return lib
 
 
-def test_bitsliced_scatter_equals_table(host_scatter, oracle_mod):
-    tables = [oracle_mod.table(0), oracle_mod.table(1)]
+@pytest.mark.parametrize("rules,mask", [(2, 0xFFFFFFFF), (1, 0)])
+def test_bitsliced_scatter_equals_table(host_scatter, oracle_mod, rules, mask):
+    tables = [oracle_mod.table(0, rules=rules), oracle_mod.table(1, rules=rules)]
     states = np.arange(256, dtype=np.uint32)
     # 8 words x 32 nodes cover all 256 bytes; a chirality pattern per run
     for chi_pattern in (0x00000000, 0xFFFFFFFF, 0xA5A5A5A5, 0x0F0F33CC):
@@ -37,7 +39,7 @@ def test_bitsliced_scatter_equals_table(host_scatter, oracle_mod):
                                for k in range(7)], dtype=np.uint32)
             solid = np.uint32(int(((nodes >> 7) & 1) @ (1 << np.arange(32, dtype=np.uint64))))
             out = np.zeros(7, dtype=np.uint32)
-            host_scatter.host_scatter_words(planes.ctypes.data, int(solid), chi_pattern, out.ctypes.data)
+            host_scatter.host_scatter_words(planes.ctypes.data, int(solid), chi_pattern, mask, out.ctypes.data)
             for j in range(32):
                 b = int(nodes[j])
                 chi = (chi_pattern >> j) & 1
