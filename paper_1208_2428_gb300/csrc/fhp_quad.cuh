@@ -55,10 +55,10 @@ __device__ __forceinline__ void collide_quad(const StepArgs& a, const StepVar& v
     uint4 gate = make_uint4(0u, 0u, 0u, 0u);
     if (FORCE) gate = rng_block((uint32_t)q, (uint32_t)(y + a.y_base), v.t_lo, v.t_hi, 1u, a.key);
 
-#define FHP_WORD(J, C)                                                                          \
+#define FHP_WORD(J, C, RR)                                                                      \
     {                                                                                           \
         Planes7 in{n0.C, n1.C, n2.C, n3.C, n4.C, n5.C, i6.C};                                   \
-        Planes7 out = scatter(in, SOLID ? sd.C : 0u, chi.C, a.rest_rules);                      \
+        Planes7 out = scatter(in, SOLID ? sd.C : 0u, chi.C, RR);                                \
         if (FORCE) {                                                                            \
             const uint32_t cand = (SOLID ? ~sd.C : 0xFFFFFFFFu) & out.m5 & ~out.m2;             \
             const uint32_t u = gate.C;                                                          \
@@ -75,10 +75,19 @@ __device__ __forceinline__ void collide_quad(const StepArgs& a, const StepVar& v
         o[0].C = out.m0; o[1].C = out.m1; o[2].C = out.m2; o[3].C = out.m3;                     \
         o[4].C = out.m4; o[5].C = out.m5; o[6].C = out.rest;                                    \
     }
-    FHP_WORD(0, x)
-    FHP_WORD(1, y)
-    FHP_WORD(2, z)
-    FHP_WORD(3, w)
+    // The rule set is uniform over a launch (and a batch tile): one branch
+    // selects code in which the rest-particle mask is a constant.
+    if (a.rest_rules != 0u) {
+        FHP_WORD(0, x, 0xFFFFFFFFu)
+        FHP_WORD(1, y, 0xFFFFFFFFu)
+        FHP_WORD(2, z, 0xFFFFFFFFu)
+        FHP_WORD(3, w, 0xFFFFFFFFu)
+    } else {
+        FHP_WORD(0, x, 0u)
+        FHP_WORD(1, y, 0u)
+        FHP_WORD(2, z, 0u)
+        FHP_WORD(3, w, 0u)
+    }
 #undef FHP_WORD
 
 }
