@@ -301,9 +301,9 @@ def serving_requests(count: int, time_scale: float = 1.0):
     from paper_1208_2428_gb300.serving import Request
     reqs = []
     for j in workloads.serving_jobs(count):
-        obst = (lambda W=j.W, H=j.H: workloads.cylinder_mask(W, H)) if j.obstacle == "cylinder" else None
-        reqs.append(Request(j.W, j.H, j.steps, seed=j.seed, density=j.density, forcing_p=j.p, obstacles=obst,
-                            cg_block=64, arrival=j.arrival * time_scale, name=j.name))
+        shapes = workloads.cylinder_shapes(j.W, j.H) if j.obstacle == "cylinder" else None
+        reqs.append(Request(j.W, j.H, j.steps, seed=j.seed, density=j.density, forcing_p=j.p,
+                            obstacle_shapes=shapes, cg_block=64, arrival=j.arrival * time_scale, name=j.name))
     return reqs
 
 
@@ -349,7 +349,7 @@ def run_serving(args):
     alg_bytes = r["issued_site_updates"] * 1.75 + r["issued_solid_site_updates"] * 0.125
     achieved = alg_bytes / (r["device_ms"] / 1e3) / 1e9 if r["device_ms"] > 0 else 0.0
     served = r["served"]
-    h2d = sum(q.width * q.height for q in reqs if q.obstacles is not None)
+    h2d = sum(16 * len(q.obstacle_shapes or []) + 64 for q in reqs)   # shapes and request parameters
     d2h = sum((q.width // q.cg_block) * (q.height // q.cg_block) * 48 for q in reqs)
     value = served["gsups"]
     line = {

@@ -160,6 +160,23 @@ FHP_API int fhp_set_forcing(fhp_lattice* lattice, double p);
  * Results are identical for every value.  Default 1. */
 FHP_API int fhp_set_temporal_block(fhp_lattice* lattice, int32_t k);
 
+/* Obstacles generated on the device from simple shapes (the walls and
+ * cylinder of the paper's flows, Section 4), so no H x W mask crosses the
+ * bus.  A node (x, y) (array indices) is solid if any shape covers it:
+ *   FHP_SHAPE_DISC: (x - a)^2 + (y - b)^2 <= c^2;
+ *   FHP_SHAPE_ROWS: a <= y < b (c unused).
+ * Replaces the solid map and clears the particles of solid nodes, as
+ * fhp_load_obstacles does with the equivalent mask.  At most
+ * FHP_MAX_SHAPES shapes; FHP_EINVAL otherwise or for an unknown kind. */
+#define FHP_SHAPE_DISC 1
+#define FHP_SHAPE_ROWS 2
+#define FHP_MAX_SHAPES 8
+typedef struct fhp_shape {
+    int32_t kind;
+    int32_t a, b, c;
+} fhp_shape;
+FHP_API int fhp_load_obstacle_shapes(fhp_lattice* lattice, const fhp_shape* shapes, int32_t count);
+
 /* Collision rule set (the paper's Fig. 2 is not legible; the default is
  * FHP-II).  FHP_RULES_FHP_II: two-body head-on collisions turned by +-60
  * degrees by the node's chirality bit, symmetric three-body collisions, and
@@ -240,6 +257,14 @@ FHP_API int fhp_synchronize(fhp_lattice* lattice);
 /* Number of kernel launches this lattice has issued since creation. */
 FHP_API int64_t fhp_kernel_launches(const fhp_lattice* lattice);
 
+/* Diagnostic (no counterpart in the paper): runs the library's two bounded
+ * device-side wait helpers -- an mbarrier phase wait and a completion-counter
+ * wait -- on conditions that never hold, on the current device.  Each gives
+ * up after its limit (2 s), so the call takes about 4 s; *host_status gets
+ * bit 0 if the barrier wait gave up and bit 1 if the counter wait did (3
+ * when the timeout path works).  The device stays usable afterwards. */
+FHP_API int fhp_selftest_wait_limits(uint32_t* host_status);
+
 /* Diagnostic: Philox4x32-10 (Salmon et al., SC'11) evaluated by the
  * library's device code.  device_ctr holds n counters of 4 words,
  * device_key n keys of 2 words, device_out receives n blocks of 4 words.
@@ -284,9 +309,17 @@ FHP_API int fhp_batch_add(fhp_batch* batch, int32_t width, int32_t height, uint6
                           int32_t* slot);
 /* Remove a member and return its memory to the arena (waits for queued work). */
 FHP_API int fhp_batch_remove(fhp_batch* batch, int32_t slot);
+/* As fhp_batch_remove without waiting: the block returns to the arena at
+ * once and any later use of it is queued on the batch's stream behind the
+ * work already there.  Work the caller queued on other streams that reads the
+ * member (fhp_batch_coarse_grain_device) must have finished. */
+FHP_API int fhp_batch_remove_async(fhp_batch* batch, int32_t slot);
 
 /* Generated initial state of a member (as fhp_init_random). */
 FHP_API int fhp_batch_init_random(fhp_batch* batch, int32_t slot, double density);
+/* Obstacles of a member from shapes (as fhp_load_obstacle_shapes);
+ * asynchronous on the batch's stream. */
+FHP_API int fhp_batch_load_obstacle_shapes(fhp_batch* batch, int32_t slot, const fhp_shape* shapes, int32_t count);
 /* Collision rule set of a member (as fhp_set_rules). */
 FHP_API int fhp_batch_set_rules(fhp_batch* batch, int32_t slot, int32_t rules);
 /* Obstacles of a member (as fhp_load_obstacles), H x W bytes, nonzero =
@@ -340,6 +373,16 @@ FHP_API int32_t fhp_batch_tile_count(fhp_batch* batch);
  * captured once and survives members joining and leaving (it is captured
  * again only when the descriptor tables grow). */
 FHP_API int fhp_batch_set_graph_steps(fhp_batch* batch, int32_t steps);
+
+/* Coarse-grain one member into device buffers ([H/B][W/B][9] int32 counts,
+ * [H/B][W/B] float rho, ux, uy; all required) on the caller's `stream`
+ * (cudaStream_t, NULL = legacy default), asynchronously.  It reads the
+ * member's current state: the caller orders the stream after the work that
+ * produced it (for example an event recorded on the batch's stream after the
+ * step call) and keeps later steps of the member from overlapping (a member
+ * whose step budget is spent is not touched by fhp_batch_step). */
+FHP_API int fhp_batch_coarse_grain_device(fhp_batch* batch, int32_t slot, int32_t block, int32_t* device_counts,
+                                          float* device_rho, float* device_ux, float* device_uy, void* stream);
 
 /* Coarse-grain one member into host buffers (as fhp_coarse_grain). */
 FHP_API int fhp_batch_coarse_grain(fhp_batch* batch, int32_t slot, int32_t block, int32_t* host_counts,

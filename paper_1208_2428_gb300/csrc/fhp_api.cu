@@ -340,6 +340,38 @@ int fhp_load_obstacles(fhp_lattice* h, const uint8_t* host_mask) {
     return read_solid_flag(h);
 }
 
+namespace {
+// Validates and copies shapes; returns false (with the lattice's message) if invalid.
+bool shape_list(const fhp_shape* shapes, int32_t count, fhp::ShapeList* out, bool* any) {
+    if (count < 0 || count > FHP_MAX_SHAPES || (count > 0 && !shapes)) return false;
+    out->n = count;
+    *any = false;
+    for (int i = 0; i < count; ++i) {
+        const fhp_shape& s = shapes[i];
+        if (s.kind != FHP_SHAPE_DISC && s.kind != FHP_SHAPE_ROWS) return false;
+        if (s.kind == FHP_SHAPE_DISC && s.c < 0) return false;
+        out->s[i] = fhp::Shape{s.kind, s.a, s.b, s.c};
+    }
+    return true;
+}
+}  // namespace
+
+int fhp_load_obstacle_shapes(fhp_lattice* h, const fhp_shape* shapes, int32_t count) {
+    if (!h) return fail(nullptr, FHP_EINVAL, "lattice is NULL");
+    fhp::ShapeList list{};
+    bool any;
+    if (!shape_list(shapes, count, &list, &any))
+        return fail(h, FHP_EINVAL, "invalid shape list (count %d, at most %d, kinds DISC or ROWS)", count,
+                    FHP_MAX_SHAPES);
+    DeviceGuard dg(h->device);
+    cudaError_t e = cudaMemsetAsync(h->flags, 0, sizeof(unsigned int), h->stream);
+    if (e == cudaSuccess)
+        e = fhp::launch_obstacle_shapes(h->g, list, h->buf[h->cur], h->solid, h->flags, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "generating obstacles");
+    ++h->launches;
+    return read_solid_flag(h);
+}
+
 int fhp_init_random(fhp_lattice* h, double density) {
     if (!h) return fail(nullptr, FHP_EINVAL, "lattice is NULL");
     if (!(density >= 0.0 && density <= 1.0)) return fail(h, FHP_EINVAL, "density %g outside [0, 1]", density);

@@ -732,6 +732,33 @@ int fhp_batch_remove(fhp_batch* b, int32_t slot) {
     return FHP_OK;
 }
 
+int fhp_batch_remove_async(fhp_batch* b, int32_t slot) {
+    Member* m = member(b, slot);
+    if (!m) return bfail(b, FHP_EINVAL, "no member in slot %d", slot);
+    // No wait: any later use of the block is enqueued on the batch's stream
+    // behind the work already there.
+    b->arena.release(m->off, m->bytes);
+    *m = Member();
+    b->tiles_dirty = true;
+    return FHP_OK;
+}
+
+int fhp_batch_coarse_grain_device(fhp_batch* b, int32_t slot, int32_t block, int32_t* counts, float* rho, float* ux,
+                                  float* uy, void* stream) {
+    Member* m = member(b, slot);
+    if (!m) return bfail(b, FHP_EINVAL, "no member in slot %d", slot);
+    if (!counts || !rho || !ux || !uy) return bfail(b, FHP_EINVAL, "NULL output buffer");
+    if (block < 32 || block % 32 || m->g.W % block || m->g.H % block)
+        return bfail(b, FHP_EINVAL, "coarse-grain block %d must be a multiple of 32 dividing %d and %d", block,
+                     m->g.W, m->g.H);
+    DeviceGuard dg(b->device);
+    cudaError_t e = fhp::launch_coarse_grain(m->g, m->buf[m->cur], m->solid, m->has_solid, block, counts, rho, ux, uy,
+                                             (cudaStream_t)stream);
+    if (e != cudaSuccess) return bcuda(b, e, "launching the coarse-grain kernel");
+    ++b->launches;
+    return FHP_OK;
+}
+
 int fhp_batch_set_state(fhp_batch* b, int32_t slot, const uint8_t* host_bytes) {
     Member* m = member(b, slot);
     if (!m || !host_bytes) return bfail(b, FHP_EINVAL, "invalid slot %d or NULL bytes", slot);
@@ -784,6 +811,44 @@ int fhp_batch_load_obstacles(fhp_batch* b, int32_t slot, const uint8_t* host_mas
         e = fhp::launch_load_obstacles(m->g, staging, m->buf[m->cur], m->solid, m->flags, b->stream);
     b->arena.release(off, n);
     if (e != cudaSuccess) return bcuda(b, e, "loading a member's obstacles");
+    ++b->launches;
+    m->has_solid = any;
+    return FHP_OK;
+}
+
+int fhp_batch_load_obstacle_shapes(fhp_batch* b, int32_t slot, const fhp_shape* shapes, int32_t count) {
+    Member* m = member(b, slot);
+    if (!m) return bfail(b, FHP_EINVAL, "no member in slot %d", slot);
+    if (count < 0 || count > FHP_MAX_SHAPES || (count > 0 && !shapes))
+        return bfail(b, FHP_EINVAL, "invalid shape list (count %d)", count);
+    fhp::ShapeList list{};
+    list.n = count;
+    for (int i = 0; i < count; ++i) {
+        const fhp_shape& sh = shapes[i];
+        if ((sh.kind != FHP_SHAPE_DISC && sh.kind != FHP_SHAPE_ROWS) || (sh.kind == FHP_SHAPE_DISC && sh.c < 0))
+            return bfail(b, FHP_EINVAL, "invalid shape %d", i);
+        list.s[i] = fhp::Shape{sh.kind, sh.a, sh.b, sh.c};
+    }
+    // Whether any node is solid, decided on the host from the shapes.
+    bool any = false;
+    for (int i = 0; i < count; ++i) {
+        const fhp_shape& sh = shapes[i];
+        if (sh.kind == FHP_SHAPE_ROWS) any = any || (std::max(sh.a, 0) < std::min(sh.b, m->g.H));
+        else {
+            const long long x0 = std::max<long long>((long long)sh.a - sh.c, 0);
+            const long long x1 = std::min<long long>((long long)sh.a + sh.c, m->g.W - 1);
+            const long long y0 = std::max<long long>((long long)sh.b - sh.c, 0);
+            const long long y1 = std::min<long long>((long long)sh.b + sh.c, m->g.H - 1);
+            for (long long y = y0; y <= y1 && !any; ++y) {
+                const long long dy = y - sh.b, r2 = (long long)sh.c * sh.c - dy * dy;
+                const long long dx = sh.a < x0 ? x0 - sh.a : (sh.a > x1 ? sh.a - x1 : 0);
+                if (x0 <= x1 && dx * dx <= r2) any = true;
+            }
+        }
+    }
+    DeviceGuard dg(b->device);
+    cudaError_t e = fhp::launch_obstacle_shapes(m->g, list, m->buf[m->cur], m->solid, nullptr, b->stream);
+    if (e != cudaSuccess) return bcuda(b, e, "generating a member's obstacles");
     ++b->launches;
     m->has_solid = any;
     return FHP_OK;

@@ -126,6 +126,19 @@ cudaError_t launch_load_obstacles(const Geometry& g, const uint8_t* mask, uint32
                                   uint32_t* solid, unsigned int* device_any_solid,
                                   cudaStream_t stream);
 
+// Obstacles from shapes (kinds as FHP_SHAPE_*): replaces the solid plane and
+// clears the particles of solid nodes.  *device_any_solid (may be NULL) is
+// set nonzero if any node is solid.
+struct Shape {
+    int kind, a, b, c;
+};
+struct ShapeList {
+    Shape s[8];
+    int n;
+};
+cudaError_t launch_obstacle_shapes(const Geometry& g, const ShapeList& shapes, uint32_t* state, uint32_t* solid,
+                                   unsigned int* device_any_solid, cudaStream_t stream);
+
 // Coarse-grain over B x B blocks (B multiple of 32 dividing W and H).
 cudaError_t launch_coarse_grain(const Geometry& g, const uint32_t* state, const uint32_t* solid,
                                 bool has_solid, int B, int32_t* counts, float* rho, float* ux,

@@ -124,7 +124,50 @@ __global__ void __launch_bounds__(kBlock) init_kernel(Geometry g, uint32_t* __re
     }
 }
 
+// Obstacles from shapes: one thread per word; a node is solid if any shape
+// covers it (discs: squared distance in index coordinates, exact in 64-bit
+// integers; row bands).
+__global__ void __launch_bounds__(kBlock) shape_kernel(Geometry g, ShapeList shapes, uint32_t* __restrict__ state,
+                                                       uint32_t* __restrict__ solid, unsigned int* any_solid) {
+    const size_t total = (size_t)g.H * g.Pq;
+    for (size_t item = (size_t)blockIdx.x * blockDim.x + threadIdx.x; item < total;
+         item += (size_t)gridDim.x * blockDim.x) {
+        const int y = (int)(item / g.Pq);
+        const int w = (int)(item - (size_t)y * g.Pq);
+        uint32_t word = 0;
+        if (w < g.Wq) {
+            for (int k = 0; k < shapes.n; ++k) {
+                const Shape sh = shapes.s[k];
+                if (sh.kind == 2) {
+                    if (y >= sh.a && y < sh.b) word = 0xFFFFFFFFu;
+                } else if (sh.kind == 1) {
+                    const long long dy = (long long)y - sh.b;
+                    const long long r2 = (long long)sh.c * sh.c - dy * dy;
+                    if (r2 < 0) continue;
+                    for (int i = 0; i < 32; ++i) {
+                        const long long dx = (long long)(32 * w + i) - sh.a;
+                        if (dx * dx <= r2) word |= 1u << i;
+                    }
+                }
+            }
+        }
+        const size_t off = (size_t)y * g.Pq + w;
+        solid[off] = word;
+        if (word) {
+            for (int b = 0; b < 7; ++b) state[(size_t)b * g.plane_words + off] &= ~word;
+            if (any_solid) atomicOr(any_solid, 1u);
+        }
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_obstacle_shapes(const Geometry& g, const ShapeList& shapes, uint32_t* state, uint32_t* solid,
+                                   unsigned int* device_any_solid, cudaStream_t stream) {
+    shape_kernel<<<grid_for((size_t)g.H * g.Pq / 32 + 1), kBlock, 0, stream>>>(g, shapes, state, solid,
+                                                                               device_any_solid);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_init_random(const Geometry& g, uint32_t* state, const uint32_t* solid, bool has_solid,
                                uint64_t seed, double density, cudaStream_t stream) {

@@ -30,6 +30,21 @@ class FhpError(RuntimeError):
         self.code = code
 
 
+class _Shape(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("a", ctypes.c_int32), ("b", ctypes.c_int32), ("c", ctypes.c_int32)]
+
+
+SHAPE_DISC = 1   # (x - a)^2 + (y - b)^2 <= c^2
+SHAPE_ROWS = 2   # a <= y < b
+
+
+def _shapes(shapes):
+    arr = (_Shape * max(1, len(shapes)))()
+    for i, (kind, a, b, c) in enumerate(shapes):
+        arr[i] = _Shape(int(kind), int(a), int(b), int(c))
+    return arr, len(shapes)
+
+
 class _Params(ctypes.Structure):
     _fields_ = [("width", ctypes.c_int32), ("height", ctypes.c_int32), ("seed", ctypes.c_uint64),
                 ("forcing_p", ctypes.c_double), ("stream", ctypes.c_void_p),
@@ -78,6 +93,9 @@ def load(path: str | None = None):
         "fhp_kernel_launches": (i64, [vp]),
         "fhp_philox4x32_10_device": (ctypes.c_int, [vp, vp, vp, i64, vp]),
         "fhp_init_random": (ctypes.c_int, [vp, ctypes.c_double]),
+        "fhp_selftest_wait_limits": (ctypes.c_int, [ctypes.POINTER(ctypes.c_uint32)]),
+        "fhp_load_obstacle_shapes": (ctypes.c_int, [vp, ctypes.POINTER(_Shape), i32]),
+        "fhp_batch_load_obstacle_shapes": (ctypes.c_int, [vp, i32, ctypes.POINTER(_Shape), i32]),
         "fhp_get_temporal_block": (ctypes.c_int, [vp]),
         "fhp_set_row_offset": (ctypes.c_int, [vp, i32]),
         "fhp_set_rules": (ctypes.c_int, [vp, i32]),
@@ -89,6 +107,8 @@ def load(path: str | None = None):
         "fhp_autotune": (ctypes.c_int, [vp, i32, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
         "fhp_batch_init_random": (ctypes.c_int, [vp, i32, ctypes.c_double]),
         "fhp_batch_set_step_kernel": (ctypes.c_int, [vp, i32]),
+        "fhp_batch_remove_async": (ctypes.c_int, [vp, i32]),
+        "fhp_batch_coarse_grain_device": (ctypes.c_int, [vp, i32, i32, vp, vp, vp, vp, vp]),
         "fhp_batch_get_step_kernel": (ctypes.c_int, [vp]),
         "fhp_batch_get_tuned_kernel": (ctypes.c_int, [vp, i32]),
         "fhp_batch_tile_count": (i32, [vp]),
@@ -229,6 +249,12 @@ class Lattice:
         if m.shape != self.shape:
             raise ValueError(f"mask must be {self.shape}")
         self._check(self._lib.fhp_load_obstacles(self._h, _ptr(m)))
+
+    def load_obstacle_shapes(self, shapes):
+        """Obstacles generated on the device from (kind, a, b, c) shapes:
+        SHAPE_DISC (x-a)^2 + (y-b)^2 <= c^2, SHAPE_ROWS a <= y < b."""
+        arr, n = _shapes(shapes)
+        self._check(self._lib.fhp_load_obstacle_shapes(self._h, arr, n))
 
     def init_random(self, density: float):
         """Generated Bernoulli(density) occupation of every fluid node."""
@@ -406,9 +432,44 @@ class Batch:
         self.shapes[slot.value] = (int(height), int(width))
         return slot.value
 
-    def remove(self, slot: int):
-        self._check(self._lib.fhp_batch_remove(self._h, int(slot)))
+    def remove(self, slot: int, wait: bool = True):
+        """Return a member's memory to the arena.  wait=False does not wait for
+        queued work (see fhp_batch_remove_async)."""
+        fn = self._lib.fhp_batch_remove if wait else self._lib.fhp_batch_remove_async
+        self._check(fn(self._h, int(slot)))
         self.shapes.pop(int(slot), None)
+
+    def coarse_grain_begin(self, slot: int, block: int, after_event=None):
+        """Start reading back a member's coarse-grained fields on a side stream
+        (optionally after a torch.cuda.Event recorded on the batch's stream);
+        returns a handle for coarse_grain_finish.  Device outputs go to pinned
+        host buffers without blocking the batch's stream."""
+        torch = _torch()
+        if getattr(self, "_side", None) is None:
+            self._side = torch.cuda.Stream(device=self.device)
+        s = self._side
+        H, W = self.shapes[slot]
+        nby, nbx = H // block, W // block
+        if after_event is not None:
+            s.wait_event(after_event)
+        with torch.cuda.stream(s):
+            dev = [torch.empty((nby, nbx, 9), dtype=torch.int32, device=self.device)] + \
+                  [torch.empty((nby, nbx), dtype=torch.float32, device=self.device) for _ in range(3)]
+            self._check(self._lib.fhp_batch_coarse_grain_device(
+                self._h, int(slot), int(block), *[ctypes.c_void_p(t.data_ptr()) for t in dev],
+                ctypes.c_void_p(s.cuda_stream)))
+            host = [torch.empty(t.shape, dtype=t.dtype, pin_memory=True) for t in dev]
+            for hsrc, dsrc in zip(host, dev):
+                hsrc.copy_(dsrc, non_blocking=True)
+        return (s, dev, host)
+
+    @staticmethod
+    def coarse_grain_finish(handle):
+        """Wait for a read-back started by coarse_grain_begin; returns
+        (counts, rho, ux, uy) as numpy arrays."""
+        s, dev, host = handle
+        s.synchronize()
+        return tuple(h.numpy() for h in host)
 
     def set_state(self, slot: int, state: np.ndarray):
         s = np.ascontiguousarray(state, dtype=np.uint8)
@@ -421,6 +482,10 @@ class Batch:
 
     def set_rules(self, slot: int, rules: int):
         self._check(self._lib.fhp_batch_set_rules(self._h, int(slot), int(rules)))
+
+    def load_obstacle_shapes(self, slot: int, shapes):
+        arr, n = _shapes(shapes)
+        self._check(self._lib.fhp_batch_load_obstacle_shapes(self._h, int(slot), arr, n))
 
     def load_obstacles(self, slot: int, mask: np.ndarray):
         m = np.ascontiguousarray(mask).astype(np.uint8, copy=False)
@@ -494,6 +559,17 @@ class Batch:
     @property
     def kernel_launches(self) -> int:
         return int(self._lib.fhp_batch_kernel_launches(self._h))
+
+
+def selftest_wait_limits() -> int:
+    """Run the bounded device-side waits on conditions that never hold;
+    returns the status bits (3: both waits gave up as designed)."""
+    lib = load()
+    st = ctypes.c_uint32(0)
+    rc = lib.fhp_selftest_wait_limits(ctypes.byref(st))
+    if rc != FHP_OK:
+        raise FhpError(rc, "wait self-test failed")
+    return int(st.value)
 
 
 def philox4x32_10_device(ctr, key, stream=None):

@@ -51,6 +51,7 @@ class Request:
     arrival: float = 0.0
     name: str = ""
     keep_state: bool = False
+    obstacle_shapes: list | None = None   # (kind, a, b, c) shapes generated on the device instead of a mask
 
     @property
     def site_updates(self) -> int:
@@ -134,7 +135,7 @@ class Server:
 
     def __init__(self, hbm_budget: int, quantum_max: int = 64, quantum_min: int = 8, graph_steps: int = 16,
                  device=None, stream=None, clock: Callable[[], float] | None = None, batch=None,
-                 time_device: bool = False):
+                 time_device: bool = False, pipeline: bool = True):
         if quantum_min < 1 or quantum_max < quantum_min:
             raise ValueError("need 1 <= quantum_min <= quantum_max")
         self.batch = batch if batch is not None else Batch(hbm_budget, device=device, stream=stream)
@@ -148,10 +149,13 @@ class Server:
         self.resident: dict[int, _Resident] = {}
         self.resident_bytes = 0
         self._blocked = False
-        self._events = None
-        if time_device:             # CUDA events around every quantum on the batch's stream
-            import torch
-            self._events = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+        self.time_device = time_device
+        # Pipelining: the next quantum is queued before the previous one is
+        # waited for, and finished lattices are read back on a side stream
+        # while it runs, so the device does not idle between quanta.
+        self.pipeline = pipeline
+        self._inflight: deque = deque()   # (start event, end event, finishing slots) per issued quantum
+        self._retiring: list[int] = []    # finished slots whose read-back could not start yet
         self._virtual = False       # serve(realtime=False): the clock counts ticks
         self._vtick = 0
         self.stats = ServerStats()
@@ -224,9 +228,12 @@ class Server:
                 self.stats.admissions_deferred += 1
                 return                      # first in line waits for memory (FIFO)
             try:
-                mask = req.obstacles() if callable(req.obstacles) else req.obstacles
-                if mask is not None:
-                    b.load_obstacles(slot, mask)
+                if req.obstacle_shapes:
+                    b.load_obstacle_shapes(slot, req.obstacle_shapes)
+                else:
+                    mask = req.obstacles() if callable(req.obstacles) else req.obstacles
+                    if mask is not None:
+                        b.load_obstacles(slot, mask)
                 b.init_random(slot, req.density)
                 b.set_steps_left(slot, req.steps)
             except FhpError as e:
@@ -240,65 +247,115 @@ class Server:
             self.resident_bytes += self.batch.lattice_bytes(req.width, req.height)
         return
 
-    def _retire(self) -> list[Completion]:
+    def _event(self):
+        stream = getattr(self.batch, "stream", None)
+        if stream is None:
+            return None
+        import torch
+        ev = torch.cuda.Event(enable_timing=self.time_device)
+        ev.record(stream)
+        return ev
+
+    def _complete(self, slot: int, results, state) -> Completion:
+        r = self.resident.pop(slot)
+        req = r.request
+        self.batch.remove(slot, wait=False) if self.pipeline else self.batch.remove(slot)
+        self.resident_bytes -= self.batch.lattice_bytes(req.width, req.height)
+        counts, rho, ux, uy = results
+        c = Completion(req, counts, rho, ux, uy, state, req.arrival, r.admitted, self.now())
+        self.stats.completed += 1
+        self.stats.site_updates += req.site_updates
+        self.stats.latencies.append(c.latency)
+        return c
+
+    def _retire(self, slots: list[int], after_event=None) -> list[Completion]:
+        """Read back finished lattices (their last quantum is complete) and
+        return their memory."""
         done = []
         b = self.batch
         self._blocked = False
-        for slot in [s for s, r in self.resident.items() if r.left == 0]:
-            r = self.resident[slot]
-            req = r.request
+        handles = {}
+        if self.pipeline:
+            for slot in slots:                       # all read-backs in flight together
+                handles[slot] = b.coarse_grain_begin(slot, self.resident[slot].request.cg_block, after_event)
+        for slot in slots:
+            req = self.resident[slot].request
             try:
-                counts, rho, ux, uy = b.coarse_grain(slot, req.cg_block)
+                if self.pipeline:
+                    results = b.coarse_grain_finish(handles[slot])
+                else:
+                    results = b.coarse_grain(slot, req.cg_block)
                 state = b.get_state(slot) if req.keep_state else None
             except FhpError as e:
                 if e.code != FHP_ENOMEM:
                     raise
                 self._blocked = True        # no staging room now: read it back on a later tick
+                self._retiring.append(slot)
                 continue
-            del self.resident[slot]
-            b.remove(slot)
-            self.resident_bytes -= self.batch.lattice_bytes(req.width, req.height)
-            c = Completion(req, counts, rho, ux, uy, state, req.arrival, r.admitted, self.now())
-            self.stats.completed += 1
-            self.stats.site_updates += req.site_updates
-            self.stats.latencies.append(c.latency)
-            done.append(c)
+            done.append(self._complete(slot, results, state))
         return done
 
+    def _finish_quantum(self) -> list[Completion]:
+        """Wait for the oldest quantum in flight and retire the lattices it finished."""
+        start, end, fin = self._inflight.popleft()
+        if end is not None:
+            end.synchronize()
+            if self.time_device and start is not None:
+                self.stats.device_ms += start.elapsed_time(end)
+        else:
+            self.batch.synchronize()
+        retry, self._retiring = self._retiring, []
+        return self._retire(retry + fin, end)
+
     def tick(self) -> list[Completion]:
-        """One scheduling round: launch a quantum for the resident lattices,
-        admit waiting requests while it runs (their set-up is queued behind
-        it), wait, and retire the finished ones."""
+        """One scheduling round: queue a quantum of steps for the lattices
+        still running, admit waiting requests behind it, then wait for the
+        previous quantum (pipelined) or this one, and retire the lattices it
+        finished."""
         b = self.batch
         q = 0
-        timed = False
-        if self.resident:
-            fewest = min(r.left for r in self.resident.values())
+        running = [r for r in self.resident.values() if r.left > 0]
+        if running:
+            fewest = min(r.left for r in running)
             q = max(self.quantum_min, min(self.quantum_max, fewest))
-            launches = b.kernel_launches if self._events else 0
-            if self._events:
-                self._events[0].record(b.stream)
+            launches = b.kernel_launches if self.time_device else 0
+            start = self._event()
             b.step(q)
-            if self._events:
-                self._events[1].record(b.stream)
+            end = self._event()
+            if self.time_device:
                 self.stats.device_launches += b.kernel_launches - launches
-                timed = True
-            for r in self.resident.values():
+            fin = []
+            for slot, r in self.resident.items():
+                if r.left == 0:
+                    continue
                 k = min(q, r.left)
                 self.stats.issued_site_updates += k * r.request.width * r.request.height
                 self.stats.issued_solid_site_updates += k * r.request.width * r.request.height \
-                    if r.request.obstacles is not None else 0
+                    if (r.request.obstacles is not None or r.request.obstacle_shapes) else 0
                 r.left -= k
+                if r.left == 0:
+                    fin.append(slot)
+            self._inflight.append((start, end, fin))
+        else:
+            # Lattices admitted with no steps to run are finished as they stand.
+            fin = [slot for slot, r in self.resident.items() if r.left == 0
+                   and not any(slot in f for _, _, f in self._inflight) and slot not in self._retiring]
+            if fin:
+                self._inflight.append((None, self._event(), fin))
         self._admit()
         self.stats.peak_resident = max(self.stats.peak_resident, len(self.resident))
         self.stats.peak_resident_bytes = max(self.stats.peak_resident_bytes, self.resident_bytes)
-        b.synchronize()
-        if timed:
-            self.stats.device_ms += self._events[0].elapsed_time(self._events[1])
+        done = []
+        keep = 1 if (self.pipeline and running) else 0
+        while len(self._inflight) > keep:
+            done.extend(self._finish_quantum())
+        if not self._inflight and self._retiring:
+            done.extend(self._retire(self._retiring[:], None))
+            self._retiring = [s for s in self._retiring if s in self.resident]
         self.stats.ticks += 1
         self.stats.quantum_steps += q
         self._vtick += 1
-        return self._retire()
+        return done
 
     def serve(self, requests: list[Request], realtime: bool = True, max_ticks: int | None = None) -> list[Completion]:
         """Serve a trace: each request is submitted once the clock passes its
@@ -345,9 +402,12 @@ def serve_sequential(requests: list[Request], realtime: bool = True, device=None
                 time.sleep(wait)
         start = (clock() - t0) if realtime else float(max(tick, req.arrival))
         with Lattice(req.width, req.height, seed=req.seed, forcing_p=req.forcing_p, device=device) as lat:
-            mask = req.obstacles() if callable(req.obstacles) else req.obstacles
-            if mask is not None:
-                lat.load_obstacles(mask)
+            if req.obstacle_shapes:
+                lat.load_obstacle_shapes(req.obstacle_shapes)
+            else:
+                mask = req.obstacles() if callable(req.obstacles) else req.obstacles
+                if mask is not None:
+                    lat.load_obstacles(mask)
             lat.init_random(req.density)
             lat.step(req.steps)
             counts, rho, ux, uy = lat.coarse_grain(req.cg_block)

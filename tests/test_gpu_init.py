@@ -84,3 +84,61 @@ def test_init_rejects_bad_density(pkg):
         for bad in (-0.1, 1.5, float("nan")):
             with pytest.raises(pkg.FhpError):
                 lat.init_random(bad)
+
+
+def shape_mask(W, H, shapes):
+    """The nodes the shapes cover, written out on the host (index coordinates)."""
+    yy, xx = np.mgrid[0:H, 0:W]
+    m = np.zeros((H, W), dtype=bool)
+    for kind, a, b, c in shapes:
+        if kind == 2:
+            m |= (yy >= a) & (yy < b)
+        else:
+            m |= (xx - a) ** 2 + (yy - b) ** 2 <= c * c
+    return m
+
+
+SHAPE_CASES = [
+    (512, 256, workloads.cylinder_shapes(512, 256)),
+    (160, 66, [(1, -5, 10, 12), (1, 170, 60, 9), (2, -3, 2, 0), (2, 60, 99, 0)]),   # shapes past the edges
+    (4128, 32, [(1, 4127, 16, 40), (1, 0, 0, 0)]),                                  # a one-node disc
+    (96, 8, []),                                                                    # no shape: no solid node
+]
+
+
+@pytest.mark.parametrize("W,H,shapes", SHAPE_CASES)
+def test_obstacle_shapes_equal_the_mask(pkg, oracle_mod, W, H, shapes):
+    mask = shape_mask(W, H, shapes)
+    if shapes == workloads.cylinder_shapes(W, H):
+        assert np.array_equal(mask, workloads.cylinder_mask(W, H))
+    s0 = workloads.bernoulli_lattice(W, H, 0.3, 5)
+    with pkg.Lattice(W, H, seed=5, forcing_p=0.01) as lat:
+        lat.set_state(s0)
+        lat.load_obstacle_shapes(shapes)
+        got = lat.get_state()
+        lat.step(7)
+        after = lat.get_state()
+    want = s0.copy()
+    want[mask] = 0x80
+    assert np.array_equal(got, want)
+    ref, _ = oracle_mod.run(want, 5, 0, 7, 0.01)
+    assert np.array_equal(after, ref)
+    # the batch version, with the state drawn after the obstacles
+    with pkg.Batch(pkg.Batch.lattice_bytes(W, H) + (8 << 20)) as b:
+        k = b.add(W, H, 9, 0.0)
+        b.load_obstacle_shapes(k, shapes)
+        b.init_random(k, 0.4)
+        b.step(5)
+        s_init = oracle_mod.init_random(W, H, 9, 0.4, mask.astype(np.uint8))
+        ref_b, _ = oracle_mod.run(s_init, 9, 0, 5, 0.0)
+        assert np.array_equal(b.get_state(k), ref_b)
+
+
+def test_obstacle_shapes_reject_bad_lists(pkg):
+    with pkg.Lattice(64, 8) as lat:
+        with pytest.raises(pkg.FhpError):
+            lat.load_obstacle_shapes([(3, 0, 0, 0)])
+        with pytest.raises(pkg.FhpError):
+            lat.load_obstacle_shapes([(1, 0, 0, -1)])
+        with pytest.raises(pkg.FhpError):
+            lat.load_obstacle_shapes([(2, 0, 1, 0)] * 9)

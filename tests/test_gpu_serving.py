@@ -30,17 +30,25 @@ def mixed_requests(serving, n, seed):
         W = int(rng.choice(np.arange(64, 449, 64)))
         H = int(rng.choice(np.arange(64, 321, 64)))
         cyl = i % 2 == 0
+        shapes = cyl and i % 4 == 0            # half of the cylinders generated on the device
         reqs.append(serving.Request(
             W, H, int(rng.integers(0, 70)), seed=880_000 + 7 * i, density=float(rng.uniform(0.1, 0.4)),
             forcing_p=5e-4 if cyl else 0.0,
-            obstacles=(lambda W=W, H=H: workloads.cylinder_mask(W, H)) if cyl else None,
+            obstacles=(lambda W=W, H=H: workloads.cylinder_mask(W, H)) if cyl and not shapes else None,
+            obstacle_shapes=workloads.cylinder_shapes(W, H) if shapes else None,
             cg_block=32, arrival=float(rng.integers(0, 12)), name=f"q{i}", keep_state=True))
     return reqs
 
 
+def request_mask(req):
+    if req.obstacle_shapes:
+        return workloads.cylinder_mask(req.width, req.height)   # the shapes used here are the cylinder's
+    return req.obstacles() if callable(req.obstacles) else req.obstacles
+
+
 def alone(pkg, req):
     with pkg.Lattice(req.width, req.height, seed=req.seed, forcing_p=req.forcing_p) as lat:
-        mask = req.obstacles() if callable(req.obstacles) else req.obstacles
+        mask = request_mask(req)
         if mask is not None:
             lat.load_obstacles(mask)
         lat.init_random(req.density)
@@ -49,7 +57,7 @@ def alone(pkg, req):
 
 
 def oracle_result(oracle_mod, req):
-    mask = req.obstacles() if callable(req.obstacles) else req.obstacles
+    mask = request_mask(req)
     s0 = oracle_mod.init_random(req.width, req.height, req.seed, req.density, mask)
     out, _ = oracle_mod.run(s0, req.seed, 0, req.steps, req.forcing_p)
     return out

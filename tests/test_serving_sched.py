@@ -62,6 +62,7 @@ class FakeBatch:
 
     def step(self, n):
         self.step_calls.append(n)
+        self.log.append(("step", n))
         for m in self.members.values():
             k = n if m["left"] < 0 else min(n, m["left"])
             m["t"] += k
@@ -80,12 +81,20 @@ class FakeBatch:
         z = np.zeros((m["h"] // block, m["w"] // block), np.float32)
         return counts, z, z, z
 
+    def coarse_grain_begin(self, slot, block, after_event=None):
+        self.log.append(("read", self.members[slot]["seed"]))
+        return self.coarse_grain(slot, block)
+
+    @staticmethod
+    def coarse_grain_finish(handle):
+        return handle
+
     def get_state(self, slot):
         m = self.members[slot]
         self._stage(m["w"] * m["h"])
         return np.full((m["h"], m["w"]), m["seed"] & 0xFF, np.uint8)
 
-    def remove(self, slot):
+    def remove(self, slot, wait=True):
         m = self.members.pop(slot)
         self.used -= m["bytes"]
         self.log.append(("remove", m["seed"]))
@@ -105,10 +114,11 @@ def make_requests(n, seed=0, sides=(64, 128, 256), max_steps=50):
     return reqs
 
 
-def test_every_request_runs_exactly_its_steps():
+@pytest.mark.parametrize("pipeline", [True, False])
+def test_every_request_runs_exactly_its_steps(pipeline):
     reqs = make_requests(40)
     fake = FakeBatch(64 << 20)
-    with Server(64 << 20, quantum_max=16, quantum_min=4, batch=fake) as srv:
+    with Server(64 << 20, quantum_max=16, quantum_min=4, batch=fake, pipeline=pipeline) as srv:
         done = srv.serve(reqs, realtime=False)
     assert sorted(c.request.name for c in done) == sorted(r.name for r in reqs)
     for c in done:
@@ -120,12 +130,13 @@ def test_every_request_runs_exactly_its_steps():
     assert not fake.members and fake.used == 0
 
 
-def test_admission_is_fifo_and_within_budget():
+@pytest.mark.parametrize("pipeline", [True, False])
+def test_admission_is_fifo_and_within_budget(pipeline):
     reqs = [Request(256, 256, 30 + i, seed=i, arrival=0.0, name=f"r{i}") for i in range(12)]
     per = FakeBatch.lattice_bytes(256, 256)
     budget = 3 * per + Server.staging_bytes(reqs[0]) + (64 << 10)
     fake = FakeBatch(budget)
-    with Server(budget, quantum_max=8, quantum_min=8, batch=fake) as srv:
+    with Server(budget, quantum_max=8, quantum_min=8, batch=fake, pipeline=pipeline) as srv:
         done = srv.serve(reqs, realtime=False)
         assert srv.stats.admissions_deferred > 0
         assert srv.stats.peak_resident <= 3
@@ -166,3 +177,19 @@ def test_summary_percentiles():
     assert s["completed"] == 10
     assert s["p50_ms"] == pytest.approx(np.percentile(lat, 50) * 1e3)
     assert s["p99_ms"] <= s["max_ms"] + 1e-9
+
+
+def test_pipelined_ticks_keep_one_quantum_queued():
+    """With pipelining a tick queues the next quantum before the previous
+    one's lattices are read back: a lattice finishing in quantum k is read
+    back in tick k + 1, after quantum k + 1 was issued."""
+    reqs = [Request(64, 64, 8, seed=1, arrival=0.0), Request(64, 64, 40, seed=2, arrival=0.0)]
+    fake = FakeBatch(1 << 24)
+    with Server(1 << 24, quantum_max=8, quantum_min=8, batch=fake, pipeline=True) as srv:
+        done = srv.serve(reqs, realtime=False)
+    assert len(done) == 2
+    steps = [i for i, e in enumerate(fake.log) if e[0] == "step"]
+    read1 = fake.log.index(("read", 1))
+    assert steps[0] < steps[1] < read1          # quantum 2 was queued before request 1 was read back
+    assert ("remove", 1) in fake.log[read1:]
+    assert [c.request.seed for c in sorted(done, key=lambda c: c.finished)] == [1, 2]

@@ -56,6 +56,13 @@ def cylinder_mask(W: int, H: int, walls: bool = True) -> np.ndarray:
     return m
 
 
+def cylinder_shapes(W: int, H: int, walls: bool = True) -> list[tuple[int, int, int, int]]:
+    """The cylinder_mask geometry as (kind, a, b, c) shapes for device-side
+    generation: kind 2 = rows a <= y < b, kind 1 = disc of radius c at (a, b)."""
+    shapes = [(2, 0, 1, 0), (2, H - 1, H, 0)] if walls else []
+    return shapes + [(1, W // 4, H // 2, H // 16)]
+
+
 def random_points(W: int, H: int, frac: float, rng: np.random.Generator) -> np.ndarray:
     """Each node solid independently with probability ``frac``."""
     return rng.random((H, W)) < frac
