@@ -57,6 +57,8 @@ def parse_args():
     ap.add_argument("--lattice-steps", type=int, default=None,
                     help="time steps per benchmark step (default: the workload's run length)")
     ap.add_argument("--temporal-block", type=int, default=1)
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the automatic kernel choice instead of timing the configurations first")
     ap.add_argument("--step-kernel", type=int, default=0,
                     help="0 auto, 1 direct, 2 bulk-copy ring, 3 multi-step ring")
     ap.add_argument("--cg-block", type=int, default=32)
@@ -446,6 +448,10 @@ def run_gpu(args):
     lat.set_state(s0)
     lat.set_temporal_block(args.temporal_block)
     lat.set_step_kernel(args.step_kernel)
+    tuned = None
+    if not args.no_autotune and args.step_kernel == 0 and args.temporal_block == 1:
+        tuned = lat.autotune(128)  # untimed: the kernel / temporal block used below
+    k_block = lat.temporal_block
     nby, nbx = (job.H // B, job.W // B) if B else (1, 1)
     counts = torch.empty((nby, nbx, 9), dtype=torch.int32, device=dev)
     rho = torch.empty((nby, nbx), dtype=torch.float32, device=dev)
@@ -491,6 +497,8 @@ def run_gpu(args):
     clocks = sampler.stop()
     kernel_name = {1: "fhp_step_direct_kernel", 2: "fhp_step_tma_kernel", 3: "fhp_run_kernel"}.get(
         lat.step_kernel, "?")
+    if k_block > 1:
+        kernel_name = f"fhp_block_kernel (k={k_block})"
     total_ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
     step_kernel_ms = sum(s.elapsed_time(m) for s, m in zip(starts, mids))
     if dist:
@@ -508,10 +516,12 @@ def run_gpu(args):
     step_launches = max(1, launches - cg_launches)
     steps_per_launch = nsteps * args.steps / step_launches
     launch_s = step_kernel_ms / 1e3 / step_launches
-    bytes_per_launch = bytes_per_node * nodes * steps_per_launch
+    # A temporally blocked pass reads and writes the state once for k steps.
+    bytes_per_launch = bytes_per_node * nodes * steps_per_launch / k_block
     achieved = bytes_per_launch / launch_s / 1e9
     peak, peak_src = measured_hbm_peak()
-    traffic = recorded_traffic(job.name, steps_per_launch)
+    # The committed capture is of the multi-step kernel.
+    traffic = recorded_traffic(job.name, steps_per_launch) if (lat.step_kernel == 3 and k_block == 1) else None
 
     # End to end through the C ABI with host buffers: pinned initial state in,
     # coarse-grained fields out, host<->device copies inside the timed region.
@@ -572,7 +582,8 @@ def run_gpu(args):
             "data": "synthetic (seeded Bernoulli lattice, index-coordinate cylinder)",
             "config": {"workload": job.name, "W": job.W, "H": job.H, "lattice_steps_per_step": nsteps,
                        "coarse_grain_block": B, "forcing_p": job.p, "density": job.density,
-                       "seed": job.seed, "temporal_block": args.temporal_block,
+                       "seed": job.seed, "temporal_block": k_block,
+                       "autotuned": {"kernel": tuned[0], "temporal_block": tuned[1]} if tuned else None,
                        "step_kernel": kernel_name,
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                        "l2": "flushed (512 MB write) before every timed step; the 120 MB working "

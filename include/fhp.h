@@ -237,8 +237,8 @@ FHP_API int fhp_autotune(fhp_lattice* lattice, int32_t trial_steps, int32_t* out
  * cp.async.bulk, one launch per step), 3 = multi-step ring (the ring kernel
  * running all steps of an fhp_step call in one cooperative launch, each tile
  * waiting only for the three tiles of the previous step it reads).  2 and 3
- * fall back to 1 when a row does not fit a stage; automatic picks 1 below
- * two tiles per SM, 3 up to 24 tiles per SM and 2 above.  Results are identical for
+ * fall back to 1 when a row does not fit a stage; automatic picks 1 for
+ * lattices of fewer than 8 tiles, 3 up to 24 tiles per SM and 2 above.  Results are identical for
  * every choice.  While the kernel is automatic and the temporal block 1, a
  * configuration recorded by fhp_autotune for the lattice's description takes
  * precedence. */
