@@ -495,8 +495,8 @@ def run_gpu(args):
         dist.barrier()
     launches = lat.kernel_launches - launches0
     clocks = sampler.stop()
-    kernel_name = {1: "fhp_step_direct_kernel", 2: "fhp_step_tma_kernel", 3: "fhp_run_kernel"}.get(
-        lat.step_kernel, "?")
+    kernel_name = {1: "fhp_step_direct_kernel", 2: "fhp_step_tma_kernel", 3: "fhp_run_kernel",
+                   4: "fhp_resident_kernel"}.get(lat.step_kernel, "?")
     if k_block > 1:
         kernel_name = f"fhp_block_kernel (k={k_block})"
     total_ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))

@@ -231,7 +231,10 @@ FHP_API int fhp_get_temporal_block(const fhp_lattice* lattice);
 FHP_API int fhp_autotune(fhp_lattice* lattice, int32_t trial_steps, int32_t* out_kernel,
                          int32_t* out_temporal_block);
 
-/* Step kernel used by fhp_step: 0 = automatic (default), 1 = direct (one
+/* Step kernel used by fhp_step: 0 = automatic (default), 4 = shared-memory
+ * resident (the lattice is cut into one strip per SM and stays in shared
+ * memory for all steps of a call; only the strips' edge rows are exchanged
+ * between steps -- for lattices whose strips fit, else as 0), 1 = direct (one
  * 128-node quad per thread, operands loaded into registers), 2 = bulk-copy
  * ring (persistent CTAs stage tiles of full rows in shared memory with
  * cp.async.bulk, one launch per step), 3 = multi-step ring (the ring kernel
@@ -245,7 +248,7 @@ FHP_API int fhp_autotune(fhp_lattice* lattice, int32_t trial_steps, int32_t* out
 FHP_API int fhp_set_step_kernel(fhp_lattice* lattice, int32_t kind);
 
 /* The step kernel fhp_step will run for the lattice's current settings
- * (1, 2 or 3), or -1 for a NULL lattice. */
+ * (1, 2, 3 or 4), or -1 for a NULL lattice. */
 FHP_API int fhp_get_step_kernel(const fhp_lattice* lattice);
 
 /* Block the calling thread until all work queued on the lattice's stream

@@ -73,7 +73,9 @@ struct TileArgs {
 // fit a stage).  Automatic picks the ring when it gets >= 2 tiles per SM.
 // kStepRun: the ring kernel running many steps in one cooperative launch
 // (per-tile dependency counters instead of a launch per step).
-enum StepKernel { kStepAuto = 0, kStepDirect = 1, kStepRing = 2, kStepRun = 3 };
+// kStepResident: lattices that fit in the SMs' shared memory stay on chip for
+// all steps of a call (fhp_resident.cu).
+enum StepKernel { kStepAuto = 0, kStepDirect = 1, kStepRing = 2, kStepRun = 3, kStepResident = 4 };
 
 // Launch one time step (motion, scattering, bounce-back, forcing).
 // `err` (device word, may be NULL) is set nonzero if a bounded wait gives up.
@@ -96,6 +98,17 @@ int run_tiles(const Geometry& g, bool has_solid);
 cudaError_t launch_run(const Geometry& g, uint32_t* buf0, uint32_t* buf1, const uint32_t* solid,
                        bool has_solid, bool force, const ForcingTable& ft, Key2 key, uint64_t t0,
                        int nsteps, unsigned int* done, cudaStream_t stream, unsigned int* err);
+
+// Shared-memory resident lattices: supported when every SM's strip (one CTA
+// per SM, at most one per row) fits in shared memory and the exchange rows fit
+// the lattice's byte-staging area (`staging_bytes`).  n >= 1 steps from buf0
+// (state at t0); the result is in buf0 if n is even, else in buf1.  `halo`
+// needs resident_halo_words() words, `flags` one word per SM (both scratch).
+bool resident_supported(const Geometry& g, bool has_solid, size_t staging_bytes);
+size_t resident_halo_words(const Geometry& g);
+cudaError_t launch_resident(const Geometry& g, uint32_t* buf0, uint32_t* buf1, const uint32_t* solid, bool has_solid,
+                            bool force, const ForcingTable& ft, Key2 key, uint64_t t0, int nsteps, uint32_t* halo,
+                            unsigned int* flags, cudaStream_t stream, unsigned int* err);
 
 // Temporal blocking: k (2, 4 or 8) steps from src (state at t0) to dst in one
 // pass.  Supported when rows are whole quads (W multiple of 128), there are

@@ -279,7 +279,8 @@ class Lattice:
         self._check(self._lib.fhp_set_temporal_block(self._h, int(k)))
 
     def set_step_kernel(self, kind: int):
-        """0 automatic, 1 direct register loads, 2 bulk-copy shared-memory ring."""
+        """0 automatic, 1 direct register loads, 2 bulk-copy shared-memory ring, 3 multi-step ring,
+        4 shared-memory resident lattice."""
         self._check(self._lib.fhp_set_step_kernel(self._h, int(kind)))
 
     # -- collision rules -------------------------------------------------------------

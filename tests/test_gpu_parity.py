@@ -65,7 +65,9 @@ SHAPES = [
 ]
 
 
-KERNELS = [1, 2, 3]   # direct register loads; bulk-copy ring; multi-step ring (one launch)
+# direct register loads; bulk-copy ring; multi-step ring (one launch); shared-memory resident lattice
+# (falls back to the automatic choice where the strips do not fit)
+KERNELS = [1, 2, 3, 4]
 
 
 @pytest.mark.parametrize("kernel", KERNELS)
@@ -100,7 +102,7 @@ def test_parity_empty_and_full(fhp_mod, oracle_mod, kernel):
         assert_same(gpu_run(fhp_mod, s0, 3, 0, 4, 0.5, kernel=kernel), want, "all solid")
 
 
-@pytest.mark.parametrize("kernel", [2, 3])
+@pytest.mark.parametrize("kernel", [2, 3, 4])
 @pytest.mark.parametrize("W,H", [(256, 2048), (4096, 1024), (2048, 512), (96, 4096), (4128, 6000)])
 def test_parity_ring_many_tiles(fhp_mod, oracle_mod, W, H, kernel):
     """Shapes where the ring kernels walk many tiles per CTA (pipeline wrap-around,
@@ -359,3 +361,24 @@ def test_fhp1_batch_member(fhp_mod, oracle_mod):
     with fhp_mod.Lattice(W, H) as lat:
         with pytest.raises(fhp_mod.FhpError):
             lat.set_rules(3)
+
+
+@pytest.mark.parametrize("W,H,steps", [(4096, 1024, 1), (4096, 1024, 2), (4096, 1024, 37), (2048, 512, 40),
+                                       (256, 2048, 9), (96, 4096, 8), (512, 150, 11), (640, 2, 5), (32, 2, 6)])
+def test_resident_kernel(fhp_mod, oracle_mod, W, H, steps):
+    """The shared-memory resident kernel (one strip per SM, edge rows exchanged
+    between steps): odd and even step counts (the result buffer alternates),
+    strips of one row, more SMs than rows, walls, a cylinder, forcing."""
+    seed = 77 + W + H
+    s0 = workloads.bernoulli_lattice(W, H, 0.3, seed, workloads.cylinder_mask(W, H) if H >= 16 else None)
+    want, _ = oracle_mod.run(s0, seed, 5, steps, 0.02)
+    with fhp_mod.Lattice(W, H, seed=seed, forcing_p=0.02, step_kernel=4) as lat:
+        lat.set_state(s0)
+        lat.set_time(5)
+        assert lat.step_kernel == 4
+        lat.step(steps)
+        assert lat.t == 5 + steps
+        assert_same(lat.get_state(), want, f"resident {W}x{H} {steps} steps")
+        lat.step(3)                      # a second call continues from the result buffer
+        more, _ = oracle_mod.run(want, seed, 5 + steps, 3, 0.02)
+        assert_same(lat.get_state(), more, "resident, second call")
