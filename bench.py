@@ -497,8 +497,14 @@ def run_gpu(args):
     clocks = sampler.stop()
     kernel_name = {1: "fhp_step_direct_kernel", 2: "fhp_step_tma_kernel", 3: "fhp_run_kernel",
                    4: "fhp_resident_kernel"}.get(lat.step_kernel, "?")
-    if k_block > 1:
+    # For the resident kernel the temporal block is the exchange interval
+    # (steps between hand-offs of strip edge rows), not a blocked pass.
+    resident = lat.step_kernel == 4
+    if resident and k_block > 1:
+        kernel_name = f"fhp_resident_ghost_kernel (exchange every {k_block} steps)"
+    elif k_block > 1:
         kernel_name = f"fhp_block_kernel (k={k_block})"
+    k_pass = 1 if resident else k_block
     total_ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
     step_kernel_ms = sum(s.elapsed_time(m) for s, m in zip(starts, mids))
     if dist:
@@ -517,7 +523,7 @@ def run_gpu(args):
     steps_per_launch = nsteps * args.steps / step_launches
     launch_s = step_kernel_ms / 1e3 / step_launches
     # A temporally blocked pass reads and writes the state once for k steps.
-    bytes_per_launch = bytes_per_node * nodes * steps_per_launch / k_block
+    bytes_per_launch = bytes_per_node * nodes * steps_per_launch / k_pass
     achieved = bytes_per_launch / launch_s / 1e9
     peak, peak_src = measured_hbm_peak()
     # The committed capture is of the multi-step kernel.

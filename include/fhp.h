@@ -66,8 +66,10 @@ typedef struct fhp_params {
 
 /* Bytes of device memory one lattice of W x H nodes uses: two bit-plane
  * state buffers (7 planes each), one solid plane, H counter words for the
- * multi-step kernel, and a W*H-byte staging area for transfers and
- * coarse-grained results.  Returns 0 for invalid sizes. */
+ * multi-step kernel, and a staging area for transfers, coarse-grained
+ * results and the resident kernel's exchange rows (W*H bytes, or 144 bytes
+ * per row quad times min(H/4, 256) where that is larger, as it can be for
+ * H < 1152).  Returns 0 for invalid sizes. */
 FHP_API size_t fhp_required_bytes(int32_t width, int32_t height);
 
 /* Create a lattice on the current CUDA device with all nodes empty and

@@ -116,7 +116,11 @@ Layout layout(int32_t W, int32_t H) {
     L.flags_off = L.solid_off + L.plane_bytes;
     L.counters_off = L.flags_off + 256;  // one word per row covers any tiling
     L.staging_off = L.counters_off + round_up((size_t)H * sizeof(unsigned int), 256);
-    L.staging_bytes = round_up((size_t)W * H, 256);
+    // W*H bytes, and at least the resident kernel's exchange rows for two
+    // ghost rows per side (2 parities x 2 sides x 9 row planes of Pq words for
+    // each of up to min(H/4, 256) strips).
+    const size_t ghost_exchange = (size_t)144 * (H / 4 < 256 ? H / 4 : 256) * g.Pq;
+    L.staging_bytes = round_up((size_t)W * H > ghost_exchange ? (size_t)W * H : ghost_exchange, 256);
     L.total = L.staging_off + L.staging_bytes;
     return L;
 }
@@ -156,9 +160,10 @@ struct DeviceGuard {
 // Kernel and temporal block fhp_step uses: the lattice's own settings, or,
 // while they are automatic (kernel 0, k = 1), the configuration autotuned
 // for this shape if there is one, else the shared-memory resident kernel
-// for lattices it holds whose multi-step ring would give fewer than two
-// tiles per SM (launch-bound sizes, where it measured fastest: 1025 vs 955
-// GSUPS on 4096 x 1024, 260 vs 235 on 2048 x 512).
+// (exchanging every second step where the strips allow it) for lattices it
+// holds whose multi-step ring would give fewer than two tiles per SM
+// (launch-bound sizes, where it measured fastest: 1163 vs 957 GSUPS on
+// 4096 x 1024, 1979 vs 1573 on 4096 x 2048).
 void effective_settings(const fhp_lattice* h, int* kernel, int* k_block) {
     *kernel = h->step_kernel;
     *k_block = h->k_block;
@@ -174,8 +179,18 @@ void effective_settings(const fhp_lattice* h, int* kernel, int* k_block) {
     int dev_sms = 0;
     if (resolved == fhp::kStepRun && cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, h->device) ==
                                          cudaSuccess &&
-        tiles < 2 * dev_sms && fhp::resident_supported(h->g, h->has_solid, h->staging_bytes))
+        tiles < 2 * dev_sms && fhp::resident_supported(h->g, h->has_solid, h->staging_bytes)) {
         *kernel = fhp::kStepResident;
+        *k_block = fhp::resident_supported(h->g, h->has_solid, h->staging_bytes, 2) ? 2 : 1;
+    }
+}
+
+// Steps between exchanges of the resident kernel for these settings (2 when
+// asked for and supported, else 1), or 0 if the resident kernel does not run.
+int resident_interval(const fhp_lattice* h, int kernel, int k_block) {
+    if (kernel != fhp::kStepResident) return 0;
+    if (k_block == 2 && fhp::resident_supported(h->g, h->has_solid, h->staging_bytes, 2)) return 2;
+    return fhp::resident_supported(h->g, h->has_solid, h->staging_bytes, 1) ? 1 : 0;
 }
 
 int check_block(fhp_lattice* h, int32_t B) {
@@ -402,6 +417,27 @@ int fhp_step(fhp_lattice* h, int64_t n) {
     const fhp::Key2 key{(uint32_t)h->seed, (uint32_t)(h->seed >> 32)};
     int kernel = h->step_kernel, k_block = h->k_block;
     effective_settings(h, &kernel, &k_block);
+    const int gh = resident_interval(h, kernel, k_block);
+    if (gh > 0) {
+        // The lattice stays in shared memory for launches of up to 2^24 steps
+        // (exchange rows in the byte-staging area, step counters in the tile
+        // counters).
+        int64_t left = n;
+        while (left > 0) {
+            const int chunk = (int)(left < (1 << 24) ? left : (1 << 24));
+            cudaError_t e = fhp::launch_resident(h->g, h->buf[h->cur], h->buf[h->cur ^ 1], h->solid, h->has_solid,
+                                                 h->force, h->ft, key, (uint64_t)h->t, chunk, gh,
+                                                 reinterpret_cast<uint32_t*>(h->staging), h->tile_done, h->stream,
+                                                 h->flags + 1);
+            if (e != cudaSuccess) return cuda_fail(h, e, "launching the resident kernel");
+            ++h->launches;
+            h->cur ^= (chunk & 1);
+            h->t += chunk;
+            left -= chunk;
+        }
+        return FHP_OK;
+    }
+    if (kernel == fhp::kStepResident) kernel = fhp::kStepAuto;  // not supported for this lattice
     if (k_block > 1 && fhp::block_supported(h->g, k_block)) {
         // Temporal blocking: passes of k steps; the remainder one step at a time.
         const int k = k_block;
@@ -415,26 +451,6 @@ int fhp_step(fhp_lattice* h, int64_t n) {
             n -= k;
         }
     }
-    if (n >= 1 && kernel == fhp::kStepResident && fhp::resident_supported(h->g, h->has_solid, h->staging_bytes)) {
-        // The lattice stays in shared memory for launches of up to 2^24 steps
-        // (exchange rows in the byte-staging area, step counters in the tile
-        // counters).
-        int64_t left = n;
-        while (left > 0) {
-            const int chunk = (int)(left < (1 << 24) ? left : (1 << 24));
-            cudaError_t e = fhp::launch_resident(h->g, h->buf[h->cur], h->buf[h->cur ^ 1], h->solid, h->has_solid,
-                                                 h->force, h->ft, key, (uint64_t)h->t, chunk,
-                                                 reinterpret_cast<uint32_t*>(h->staging), h->tile_done, h->stream,
-                                                 h->flags + 1);
-            if (e != cudaSuccess) return cuda_fail(h, e, "launching the resident kernel");
-            ++h->launches;
-            h->cur ^= (chunk & 1);
-            h->t += chunk;
-            left -= chunk;
-        }
-        return FHP_OK;
-    }
-    if (kernel == fhp::kStepResident) kernel = fhp::kStepAuto;  // not supported for this lattice
     if (n >= 2 && fhp::resolved_step_kernel(h->g, h->has_solid, kernel) == fhp::kStepRun) {
         // All n steps in cooperative launches of up to 2^24 steps each.
         int64_t left = n;
@@ -598,6 +614,8 @@ int fhp_get_temporal_block(const fhp_lattice* h) {
     if (!h) return -1;
     int kernel, k_block;
     effective_settings(h, &kernel, &k_block);
+    const int gh = resident_interval(h, kernel, k_block);
+    if (gh > 0) return gh;
     return k_block > 1 && fhp::block_supported(h->g, k_block) ? k_block : 1;
 }
 
@@ -629,7 +647,8 @@ int fhp_autotune(fhp_lattice* h, int32_t trial_steps, int32_t* out_kernel, int32
         cands.push_back({fhp::kStepRing, 1});
         cands.push_back({fhp::kStepRun, 1});
     }
-    if (fhp::resident_supported(h->g, h->has_solid, h->staging_bytes)) cands.push_back({fhp::kStepResident, 1});
+    if (fhp::resident_supported(h->g, h->has_solid, h->staging_bytes, 1)) cands.push_back({fhp::kStepResident, 1});
+    if (fhp::resident_supported(h->g, h->has_solid, h->staging_bytes, 2)) cands.push_back({fhp::kStepResident, 2});
     for (int k : {2, 4, 8})
         if (fhp::block_supported(h->g, k) && trial_steps % k == 0) cands.push_back({fhp::kStepDirect, k});
     TuneChoice best{fhp::kStepDirect, 1};

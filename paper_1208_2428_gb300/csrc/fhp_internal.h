@@ -101,14 +101,17 @@ cudaError_t launch_run(const Geometry& g, uint32_t* buf0, uint32_t* buf1, const 
 
 // Shared-memory resident lattices: supported when every SM's strip (one CTA
 // per SM, at most one per row) fits in shared memory and the exchange rows fit
-// the lattice's byte-staging area (`staging_bytes`).  n >= 1 steps from buf0
+// the lattice's byte-staging area (`staging_bytes`).  `gh` is the number of
+// steps between exchanges: 1 (each strip trades its edge rows every step) or
+// 2 (each strip also computes 2 ghost rows per side itself and trades 2 rows
+// every 2 steps; needs strips of at least 4 rows).  n >= 1 steps from buf0
 // (state at t0); the result is in buf0 if n is even, else in buf1.  `halo`
 // needs resident_halo_words() words, `flags` one word per SM (both scratch).
-bool resident_supported(const Geometry& g, bool has_solid, size_t staging_bytes);
-size_t resident_halo_words(const Geometry& g);
+bool resident_supported(const Geometry& g, bool has_solid, size_t staging_bytes, int gh = 1);
+size_t resident_halo_words(const Geometry& g, int gh);
 cudaError_t launch_resident(const Geometry& g, uint32_t* buf0, uint32_t* buf1, const uint32_t* solid, bool has_solid,
-                            bool force, const ForcingTable& ft, Key2 key, uint64_t t0, int nsteps, uint32_t* halo,
-                            unsigned int* flags, cudaStream_t stream, unsigned int* err);
+                            bool force, const ForcingTable& ft, Key2 key, uint64_t t0, int nsteps, int gh,
+                            uint32_t* halo, unsigned int* flags, cudaStream_t stream, unsigned int* err);
 
 // Temporal blocking: k (2, 4 or 8) steps from src (state at t0) to dst in one
 // pass.  Supported when rows are whole quads (W multiple of 128), there are

@@ -382,3 +382,40 @@ def test_resident_kernel(fhp_mod, oracle_mod, W, H, steps):
         lat.step(3)                      # a second call continues from the result buffer
         more, _ = oracle_mod.run(want, seed, 5 + steps, 3, 0.02)
         assert_same(lat.get_state(), more, "resident, second call")
+
+
+@pytest.mark.parametrize("W,H,steps,obstacles,p", [
+    (4096, 1024, 1, True, 0.02), (4096, 1024, 2, True, 0.02), (4096, 1024, 3, True, 0.02),
+    (4096, 1024, 37, True, 0.02), (2048, 1024, 40, False, 0.0), (256, 2048, 9, True, 0.0),
+    (96, 4096, 8, False, 0.02), (512, 608, 7, True, 0.02), (160, 610, 5, True, 0.01), (4128, 640, 12, False, 0.05)])
+def test_resident_ghost_rows(fhp_mod, oracle_mod, W, H, steps, obstacles, p):
+    """The resident kernel with two ghost rows per strip side (exchanges every
+    second step): step counts that end inside a round, strips of exactly four
+    rows, ragged rows, with and without obstacles and forcing."""
+    seed = 91 + W + H
+    s0 = workloads.bernoulli_lattice(W, H, 0.3, seed, workloads.cylinder_mask(W, H) if obstacles else None)
+    want, _ = oracle_mod.run(s0, seed, 5, steps, p)
+    with fhp_mod.Lattice(W, H, seed=seed, forcing_p=p, step_kernel=4) as lat:
+        lat.set_temporal_block(2)
+        lat.set_state(s0)
+        lat.set_time(5)
+        assert lat.step_kernel == 4 and lat.temporal_block == 2
+        lat.step(steps)
+        assert lat.t == 5 + steps
+        assert_same(lat.get_state(), want, f"resident ghost {W}x{H} {steps} steps")
+        lat.step(3)
+        more, _ = oracle_mod.run(want, seed, 5 + steps, 3, p)
+        assert_same(lat.get_state(), more, "resident ghost, second call")
+
+
+def test_resident_ghost_falls_back_to_one_row(fhp_mod, oracle_mod):
+    """Strips shorter than four rows take the one-row exchange."""
+    W, H, seed = 512, 150, 4
+    s0 = workloads.bernoulli_lattice(W, H, 0.3, seed)
+    want, _ = oracle_mod.run(s0, seed, 0, 6, 0.0)
+    with fhp_mod.Lattice(W, H, seed=seed, step_kernel=4) as lat:
+        lat.set_temporal_block(2)
+        assert lat.step_kernel == 4 and lat.temporal_block == 1
+        lat.set_state(s0)
+        lat.step(6)
+        assert_same(lat.get_state(), want, "resident fallback")
