@@ -49,14 +49,9 @@ struct BatchLattice {
     unsigned long long t0;    // step counter at the start of the current call
     int cur;                  // buffer holding S_{t0}
     int steps;                // steps in the current call (0: idle)
-    int kind;                 // kKindForce | kKindSolid | kKindRagged
+    int force;
     int tile_base;            // index of the lattice's tile 0 in the tile list
 };
-
-// Member kinds: forcing on, obstacles present (the solid plane is staged and
-// bounce-back applies), rows end in a partial quad.  Each combination runs
-// its own instantiation of the per-quad code, chosen once per tile.
-constexpr int kKindForce = 1, kKindSolid = 2, kKindRagged = 4;
 
 struct BatchTile {
     int lattice;
@@ -69,7 +64,7 @@ struct __align__(16) StageHeader {
     TileArgs ta;
     int tile;
     int active;
-    int kind;
+    int force;
     int pad;
 };
 
@@ -84,7 +79,7 @@ constexpr int kBPrefixBytes = 128 + kBStages * kHeaderBytes;  // barriers, then 
 struct DescCache {
     int lat = -1;
     uint32_t dw[kDescRegs];
-    int steps = 0, cur = 0, kind = 0, tile_base = 0;
+    int steps = 0, cur = 0, force = 0, tile_base = 0;
     unsigned long long t0 = 0;
     uint32_t* buf0 = nullptr;
     uint32_t* buf1 = nullptr;
@@ -102,7 +97,7 @@ __device__ __forceinline__ void load_desc(DescCache& c, const BatchLattice* __re
     if (lane == 0) {
         c.steps = L->steps;
         c.cur = L->cur;
-        c.kind = L->kind;
+        c.force = L->force;
         c.tile_base = L->tile_base;
         c.t0 = L->t0;
         c.buf0 = L->buf[0];
@@ -134,28 +129,14 @@ __device__ __forceinline__ void write_header(StageHeader* h, const DescCache& c,
         h->ta = c.ta;
         h->tile = tile;
         h->active = s < c.steps;
-        h->kind = c.kind;
+        h->force = c.force;
     }
 }
 
-template <bool SOLID, bool FORCE, bool RAGGED>
-__device__ __forceinline__ void batch_compute_kind(const StageHeader& h, const uint32_t* stage) {
-    const StepVar v{h.a.dst, h.a.t_lo, h.a.t_hi};
-    compute_tile<SOLID, FORCE, RAGGED>(h.a, v, h.ta, h.tile, stage, (int)threadIdx.x, kBConsumerWarps * 32);
-}
-
-// The tile's member kind selects the instantiation (uniform across the CTA).
+template <bool FORCE>
 __device__ __forceinline__ void batch_compute(const StageHeader& h, const uint32_t* stage) {
-    switch (h.kind & 7) {
-        case 0: batch_compute_kind<false, false, false>(h, stage); break;
-        case kKindForce: batch_compute_kind<false, true, false>(h, stage); break;
-        case kKindSolid: batch_compute_kind<true, false, false>(h, stage); break;
-        case kKindSolid | kKindForce: batch_compute_kind<true, true, false>(h, stage); break;
-        case kKindRagged: batch_compute_kind<false, false, true>(h, stage); break;
-        case kKindRagged | kKindForce: batch_compute_kind<false, true, true>(h, stage); break;
-        case kKindRagged | kKindSolid: batch_compute_kind<true, false, true>(h, stage); break;
-        default: batch_compute_kind<true, true, true>(h, stage); break;
-    }
+    const StepVar v{h.a.dst, h.a.t_lo, h.a.t_hi};
+    compute_tile<true, FORCE, true>(h.a, v, h.ta, h.tile, stage, (int)threadIdx.x, kBConsumerWarps * 32);
 }
 
 __global__ void __launch_bounds__(kBThreads, 2)
@@ -214,10 +195,7 @@ __global__ void __launch_bounds__(kBThreads, 2)
             if (lane == 0) {
                 if (h->active) {
                     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                    if (c.kind & kKindSolid)
-                        issue_tile<true>(h->a, h->ta, h->a.src, bt_tile, stages + (size_t)st * stage_words, &full[st]);
-                    else
-                        issue_tile<false>(h->a, h->ta, h->a.src, bt_tile, stages + (size_t)st * stage_words, &full[st]);
+                    issue_tile<true>(h->a, h->ta, h->a.src, bt_tile, stages + (size_t)st * stage_words, &full[st]);
                 } else {
                     mbar_arrive_expect_tx(&full[st], 0u);  // nothing to stage: release the stage at once
                 }
@@ -240,7 +218,8 @@ __global__ void __launch_bounds__(kBThreads, 2)
         }
         const StageHeader& h = headers[st];
         if (h.active) {
-            batch_compute(h, stages + (size_t)st * stage_words);
+            if (h.force) batch_compute<true>(h, stages + (size_t)st * stage_words);
+            else batch_compute<false>(h, stages + (size_t)st * stage_words);
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[st]);
@@ -355,12 +334,8 @@ __global__ void __launch_bounds__(kBRunThreads, 2)
                 if (lane == 0) {
                     if (h->active) {
                         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                        if (c.kind & kKindSolid)
-                            issue_tile<true>(h->a, h->ta, h->a.src, bt_tile, stages + (size_t)st * stage_words,
-                                             &full[st]);
-                        else
-                            issue_tile<false>(h->a, h->ta, h->a.src, bt_tile, stages + (size_t)st * stage_words,
-                                              &full[st]);
+                        issue_tile<true>(h->a, h->ta, h->a.src, bt_tile, stages + (size_t)st * stage_words,
+                                         &full[st]);
                     } else {
                         mbar_arrive_expect_tx(&full[st], 0u);
                     }
@@ -390,7 +365,8 @@ __global__ void __launch_bounds__(kBRunThreads, 2)
             }
             const StageHeader& h = headers[st];
             if (h.active) {
-                batch_compute(h, stages + (size_t)st * stage_words);
+                if (h.force) batch_compute<true>(h, stages + (size_t)st * stage_words);
+                else batch_compute<false>(h, stages + (size_t)st * stage_words);
             }
             __syncwarp();
             if (lane == 0) {
@@ -1030,8 +1006,7 @@ int upload_descriptors(fhp_batch* b, int chunk, std::vector<int>& steps_of, int*
         L.t0 = (unsigned long long)m.t;
         L.cur = m.cur;
         L.steps = (int)k;
-        L.kind = (m.ft.q[32] != 0 ? fhp::kKindForce : 0) | (m.has_solid ? fhp::kKindSolid : 0) |
-                 (m.g.Wq % 4 != 0 ? fhp::kKindRagged : 0);
+        L.force = m.ft.q[32] != 0;
         L.tile_base = m.tile_base;
     }
     if (*max_steps == 0) return FHP_OK;
