@@ -111,7 +111,7 @@ def rng_word(seed: int, t: int, y: int, w: int, stream: int) -> int:
 
 def table(chirality: int, rules: int = 2) -> np.ndarray:
     """The 256-entry scattering table for chirality 0 or 1 (uint8[256]) of
-    rule set 2 (FHP-II) or 1 (FHP-I)."""
+    rule set 2 (FHP-II), 1 (FHP-I) or 3 (FHP-III, collision-saturated)."""
     out = np.zeros(256, dtype=np.uint8)
     if rules == 2:
         _load().oracle_build_table(int(chirality), _ptr(out, ctypes.c_uint8))
@@ -135,7 +135,7 @@ def forcing_thresholds(p: float) -> np.ndarray:
 
 def run(state: np.ndarray, seed: int, t0: int, n: int, p: float = 0.0, rules: int = 2) -> tuple[np.ndarray, int]:
     """Advance an H x W uint8 lattice by n steps from step t0 (rule set 2 =
-    FHP-II, 1 = FHP-I).
+    FHP-II, 1 = FHP-I, 3 = FHP-III).
 
     Returns (new state, number of forcing events)."""
     s = np.array(state, dtype=np.uint8, order="C", copy=True)
@@ -152,7 +152,7 @@ def run(state: np.ndarray, seed: int, t0: int, n: int, p: float = 0.0, rules: in
         ev = _load().oracle_run_rules(W, H, _ptr(s, ctypes.c_uint8), _ptr(scratch, ctypes.c_uint8),
                                       int(seed), int(t0), int(n), float(p), int(rules))
         if ev < 0:
-            raise ValueError("rules must be 1 or 2")
+            raise ValueError("rules must be 1, 2 or 3")
     return s, int(ev)
 
 

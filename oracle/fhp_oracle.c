@@ -26,7 +26,7 @@
  * Where the paper is silent (the picture of the rule set, the direction
  * numbering, the random-number source, the step order) this file follows the
  * readings listed in the design notes of the repository (R-dir, R-map,
- * R-order, R-rules, R-solid, R-rng, R-force, R-cg).
+ * R-order, R-rules, R-fhp3, R-solid, R-rng, R-force, R-cg).
  *
  * Direction numbering (R-dir): c_i points at angle (i-2)*60 degrees,
  * counter-clockwise from +x; i+3 (mod 6) is opposite to i.
@@ -105,9 +105,72 @@ ORACLE_EXPORT uint32_t oracle_rng_word(uint64_t seed, uint64_t t, int y, int w, 
 
 static int dir_bit(int i) { return 1 << (((i % 6) + 6) % 6); }
 
+/* FHP-III, the collision-saturated rule set (reading R-fhp3; the paper
+ * cites the model family but prints no table).  A fluid state (7 bits) whose
+ * mass and momentum are shared by no other state stays; every other state
+ * becomes another state of its class:
+ *   - zero momentum (head-on pairs, triples, two head-on pairs, each with or
+ *     without the rest particle): the moving particles turn by +60 degrees
+ *     (chirality 0) or -60 degrees (chirality 1);
+ *   - a class of two states (rest + i <-> {i-1, i+1}, and the particle-hole
+ *     duals of those pairs): the other state;
+ *   - a class of three states (momentum c_k, mass 3 or 4): a cycle, written
+ *     out below for momentum c_2 and turned to c_k; chirality 1 runs it
+ *     backwards.
+ * Momentum is counted in the lattice basis (c_2, c_3): c_0 = (0,-1),
+ * c_1 = (1,-1), c_2 = (1,0), c_3 = (0,1), c_4 = (-1,1), c_5 = (-1,0). */
+static void node_invariants(int s, int* mass, int* px, int* py) {
+    static const int vx[6] = {0, 1, 1, 0, -1, -1}, vy[6] = {-1, -1, 0, 1, 1, 0};
+    *mass = (s >> REST_BIT) & 1;
+    *px = *py = 0;
+    for (int i = 0; i < 6; ++i)
+        if (s & dir_bit(i)) {
+            ++*mass;
+            *px += vx[i];
+            *py += vy[i];
+        }
+}
+
+/* Moving particle i becomes i + by (mod 6); the rest bit is kept. */
+static int turn_movers(int s, int by) {
+    int out = s & (1 << REST_BIT);
+    for (int i = 0; i < 6; ++i)
+        if (s & dir_bit(i)) out |= dir_bit(i + by);
+    return out;
+}
+
+static int fhp3_scatter(int s, int chirality) {
+    int mass, px, py;
+    node_invariants(s, &mass, &px, &py);
+    int cls[128], n = 0;
+    for (int t = 0; t < 128; ++t) {
+        int m2, x2, y2;
+        node_invariants(t, &m2, &x2, &y2);
+        if (m2 == mass && x2 == px && y2 == py) cls[n++] = t;
+    }
+    if (n == 1) return s;
+    if (px == 0 && py == 0) return turn_movers(s, chirality == 0 ? 1 : 5);
+    if (n == 2) return cls[0] == s ? cls[1] : cls[0];
+    /* Three states with momentum c_k.  For k = 2 (E), chirality 0:
+     *   mass 3: E + pair {0,3} -> E + pair {1,4} -> rest + {1,3} -> back;
+     *   mass 4: rest + E + pair {1,4} -> rest + E + pair {0,3}
+     *           -> {1,3} + pair {2,5} -> back
+     * (the mass-4 cycle is the particle-hole dual of the mass-3 one). */
+    static const int cyc3[3] = {0x0D, 0x16, 0x4A}, cyc4[3] = {0x56, 0x4D, 0x2E};
+    static const int vx[6] = {0, 1, 1, 0, -1, -1}, vy[6] = {-1, -1, 0, 1, 1, 0};
+    int k = 0;
+    while (vx[k] != px || vy[k] != py) ++k;
+    const int* cyc = mass == 3 ? cyc3 : cyc4;
+    const int e = turn_movers(s, 2 - k + 6);
+    int j = 0;
+    while (cyc[j] != e) ++j;
+    return turn_movers(cyc[(j + (chirality == 0 ? 1 : 2)) % 3], k - 2 + 6);
+}
+
 /* Rule sets: 2 = FHP-II (reading R-rules), 1 = FHP-I (the original model of
  * Frisch, Hasslacher and Pomeau: head-on and symmetric three-body collisions
- * only; a rest particle, if present, is a spectator that never changes). */
+ * only; a rest particle, if present, is a spectator that never changes),
+ * 3 = FHP-III (above). */
 ORACLE_EXPORT void oracle_build_table_rules(int rules, int chirality, uint8_t table[256]) {
     for (int b = 0; b < 256; ++b) {
         int moving = b & 0x3F;
@@ -120,6 +183,8 @@ ORACLE_EXPORT void oracle_build_table_rules(int rules, int chirality, uint8_t ta
             for (int i = 0; i < 6; ++i)
                 if (moving & dir_bit(i)) reflected |= dir_bit(i + 3);
             out = (b & 0xC0) | reflected;
+        } else if (rules == 3) {
+            out = fhp3_scatter(b, chirality);
         } else {
             int done = 0;
             /* Two-body head-on: exactly the pair {i, i+3} moving (rest
@@ -297,7 +362,7 @@ ORACLE_EXPORT int64_t oracle_run(int W, int H, uint8_t* state, uint8_t* scratch,
 /* oracle_run with the rule set chosen (1 = FHP-I, 2 = FHP-II). */
 ORACLE_EXPORT int64_t oracle_run_rules(int W, int H, uint8_t* state, uint8_t* scratch, uint64_t seed, uint64_t t0,
                                        int64_t n, double p, int rules) {
-    if (rules != 1 && rules != 2) return -1;
+    if (rules < 1 || rules > 3) return -1;
     return run_rows(W, H, state, scratch, seed, t0, n, p, 0, H, rules);
 }
 

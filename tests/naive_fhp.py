@@ -59,8 +59,58 @@ def momentum(dirs) -> tuple[float, float]:
     return (sum(VEL[i][0] for i in dirs), sum(VEL[i][1] for i in dirs))
 
 
+def _byte(dirs, rest) -> int:
+    return (0x40 if rest else 0) | sum(1 << i for i in set(dirs))
+
+
+def _same_invariants(dirs, rest):
+    """Every 7-bit fluid state with the mass and (vector) momentum of this one."""
+    mass = len(dirs) + rest
+    px, py = momentum(dirs)
+    out = []
+    for b in range(128):
+        d = [i for i in range(6) if b >> i & 1]
+        qx, qy = momentum(d)
+        if len(d) + (b >> 6) == mass and abs(qx - px) < 1e-9 and abs(qy - py) < 1e-9:
+            out.append(b)
+    return out
+
+
+def scatter_saturated(dirs, rest: bool, chirality: int) -> int:
+    """FHP-III (reading R-fhp3), phrased with velocities: a state with zero
+    momentum turns its whole velocity set by 60 degrees; one that shares its
+    mass and momentum with exactly one other state becomes that state; the
+    three states of momentum c_k and mass 3 (mover k plus a head-on pair along
+    c_{k+1}, the same with the pair along c_{k+2}, rest plus movers k-1, k+1)
+    and of mass 4 (rest + mover k + pair along c_{k+2}, rest + mover k + pair
+    along c_{k+1}, movers k-1, k+1 + pair along c_k) are visited in that
+    order for chirality 0 and backwards for chirality 1."""
+    turn = 1 if chirality == 0 else -1
+    same = _same_invariants(dirs, rest)
+    if len(same) == 1:
+        return _byte(dirs, rest)
+    px, py = momentum(dirs)
+    if abs(px) < 1e-9 and abs(py) < 1e-9:
+        return _byte([rotate(i, turn) for i in dirs], rest)
+    if len(same) == 2:
+        me = _byte(dirs, rest)
+        return same[1] if same[0] == me else same[0]
+    k = direction_of(px, py)
+    def pair(j):
+        return [j, rotate(j, 3)]
+    if len(dirs) + rest == 3:
+        cycle = [_byte([k] + pair(rotate(k, 1)), False), _byte([k] + pair(rotate(k, 2)), False),
+                 _byte([rotate(k, -1), rotate(k, 1)], True)]
+    else:
+        cycle = [_byte([k] + pair(rotate(k, 2)), True), _byte([k] + pair(rotate(k, 1)), True),
+                 _byte([rotate(k, -1), rotate(k, 1)] + pair(k), False)]
+    j = cycle.index(_byte(dirs, rest))
+    return cycle[(j + turn) % 3]
+
+
 def scatter(byte: int, chirality: int, rules: int = 2) -> int:
-    """rules 2: FHP-II; rules 1: FHP-I (no rest-particle collisions)."""
+    """rules 2: FHP-II; rules 1: FHP-I (no rest-particle collisions); rules 3:
+    FHP-III (collision-saturated)."""
     solid = bool(byte & 0x80)
     rest = bool(byte & 0x40)
     dirs = [i for i in range(6) if byte >> i & 1]
@@ -68,6 +118,8 @@ def scatter(byte: int, chirality: int, rules: int = 2) -> int:
         # bounce-back: every velocity reversed
         new = [rotate(i, 3) for i in dirs]
         return 0x80 | (0x40 if rest else 0) | sum(1 << i for i in new)
+    if rules == 3:
+        return scatter_saturated(dirs, rest, chirality)
     px, py = momentum(dirs)
     zero = abs(px) < 1e-9 and abs(py) < 1e-9
     new_rest = rest

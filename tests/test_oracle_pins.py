@@ -566,3 +566,80 @@ def test_fhp1_brute_force_naive_model(oracle_mod, W, H, p):
     got, _ = oracle_mod.run(s, seed, 0, 4, p, rules=1)
     assert np.array_equal(got, cur)
     assert int(np.count_nonzero(got & 0x40)) == int(np.count_nonzero(s & 0x40))  # rest particles never move or change
+
+
+# ---------------------------------------------------------------------------
+# FHP-III rule set (reading R-fhp3: collision-saturated; every fluid state
+# that shares its mass and momentum with another state changes).
+# ---------------------------------------------------------------------------
+def _turn(b, by):
+    out = b & 0xC0
+    for i in range(6):
+        if b >> i & 1:
+            out |= 1 << ((i + by) % 6)
+    return out
+
+
+def test_fhp3_table_invariants_and_symmetries(oracle_mod):
+    t3 = [oracle_mod.table(c, rules=3) for c in (0, 1)]
+    t2 = [oracle_mod.table(c, rules=2) for c in (0, 1)]
+    for chi in (0, 1):
+        t = t3[chi]
+        assert sorted(int(v) for v in t) == list(range(256))             # a permutation
+        for b in range(256):
+            o = int(t[b])
+            assert o == naive.scatter(b, chi, rules=3), (chi, b)         # the geometric model
+            assert int(t3[1 - chi][o]) == b                              # chiralities are inverse
+            if b & 0x80:
+                assert o == int(t2[chi][b])                               # bounce-back unchanged
+                continue
+            assert o < 128 and mass(o) == mass(b)
+            assert mom(o) == pytest.approx(mom(b), abs=1e-9)
+            assert int(t[127 - b]) == 127 - o                            # particle-hole duality
+            for by in range(6):                                           # rotation covariance
+                assert int(t[_turn(b, by)]) == _turn(o, by)
+            if t2[chi][b] != b:                                           # every FHP-II collision kept
+                assert o == int(t2[chi][b]), (chi, b)
+        # saturation: a state changes iff another state has its mass and momentum
+        for b in range(128):
+            shared = any(mass(c) == mass(b) and mom(c) == pytest.approx(mom(b), abs=1e-9)
+                         for c in range(128) if c != b)
+            assert (int(t[b]) != b) == shared, b
+        assert sum(int(t[b]) != b for b in range(128)) == 76
+
+
+def test_fhp3_rule_examples(oracle_mod):
+    t0, t1 = oracle_mod.table(0, rules=3), oracle_mod.table(1, rules=3)
+    E, NE, NW, W, SW, SE, R = 1 << 2, 1 << 3, 1 << 4, 1 << 5, 1 << 0, 1 << 1, 1 << 6
+    # two head-on pairs turn like one (FHP-II leaves them alone)
+    assert t0[SW | NE | SE | NW] == SE | NW | E | W
+    assert t1[SW | NE | SE | NW] == SW | NE | E | W
+    # five movers <-> rest + four movers of the same momentum
+    assert t0[SW | SE | E | NE | NW] == R | SE | E | NE | W
+    assert t1[R | SE | E | NE | W] == SW | SE | E | NE | NW
+    # mover E with a spectator pair: the pair turns, then the rest particle appears
+    assert t0[E | SW | NE] == E | SE | NW
+    assert t0[E | SE | NW] == R | SE | NE
+    assert t0[R | SE | NE] == E | SW | NE
+    assert t1[E | SW | NE] == R | SE | NE
+    # states without a partner stay (rest + E is not one: it pairs with SE + NE)
+    assert t0[R | E] == SE | NE and t1[R | E] == SE | NE
+    for b in (0, R, E, SW | SE | E | NE | NW | W, 0x7F, E | NE):
+        assert t0[b] == b and t1[b] == b
+
+
+@pytest.mark.parametrize("W,H,p", [(32, 4, 0.0), (64, 6, 0.2)])
+def test_fhp3_brute_force_naive_model(oracle_mod, W, H, p):
+    rng = np.random.Generator(np.random.PCG64(23))
+    s = rng.integers(0, 128, size=(H, W), dtype=np.uint8)
+    s[1, 3:9] |= 0x80
+    seed, cur = 8, s.copy()
+    orig_scatter = naive.scatter
+    try:
+        naive.scatter = lambda b, c, rules=3: orig_scatter(b, c, rules=3)
+        for t in range(4):
+            cur = naive.step(cur, seed, t, p, oracle_mod.rng_word)
+    finally:
+        naive.scatter = orig_scatter
+    got, _ = oracle_mod.run(s, seed, 0, 4, p, rules=3)
+    assert np.array_equal(got, cur)
