@@ -184,10 +184,18 @@ FHP_API int fhp_load_obstacle_shapes(fhp_lattice* lattice, const fhp_shape* shap
  * degrees by the node's chirality bit, symmetric three-body collisions, and
  * rest-particle creation / annihilation (rest + c_i <-> c_{i-1} + c_{i+1}).
  * FHP_RULES_FHP_I: the original model without the rest-particle rules (a rest
- * particle, if present, is a spectator that never changes).  Takes effect
- * from the next step.  FHP_EINVAL for other values. */
+ * particle, if present, is a spectator that never changes).
+ * FHP_RULES_FHP_III: the collision-saturated set -- every fluid state that
+ * shares its mass and momentum with another state changes: zero-momentum
+ * states turn their movers by +-60 degrees (chirality), two-state classes
+ * swap, and the three-state classes of momentum c_k cycle (chirality sets the
+ * direction); it keeps every FHP-II collision.  FHP-III lattices step with
+ * the direct kernel only (the step-kernel and temporal-block settings are
+ * ignored) and cannot be batch members.  Takes effect from the next step.
+ * FHP_EINVAL for other values. */
 #define FHP_RULES_FHP_I 1
 #define FHP_RULES_FHP_II 2
+#define FHP_RULES_FHP_III 3
 FHP_API int fhp_set_rules(fhp_lattice* lattice, int32_t rules);
 FHP_API int fhp_get_rules(const fhp_lattice* lattice);
 
@@ -325,7 +333,8 @@ FHP_API int fhp_batch_init_random(fhp_batch* batch, int32_t slot, double density
 /* Obstacles of a member from shapes (as fhp_load_obstacle_shapes);
  * asynchronous on the batch's stream. */
 FHP_API int fhp_batch_load_obstacle_shapes(fhp_batch* batch, int32_t slot, const fhp_shape* shapes, int32_t count);
-/* Collision rule set of a member (as fhp_set_rules). */
+/* Collision rule set of a member (as fhp_set_rules; FHP_RULES_FHP_I or
+ * FHP_RULES_FHP_II -- FHP-III runs on single lattices only, FHP_EINVAL). */
 FHP_API int fhp_batch_set_rules(fhp_batch* batch, int32_t slot, int32_t rules);
 /* Obstacles of a member (as fhp_load_obstacles), H x W bytes, nonzero =
  * solid.  Asynchronous: the mask is copied on the batch's stream; a pageable

@@ -52,8 +52,10 @@ thread_local std::string g_create_error;
 struct TuneKey {
     int device, W, H;
     bool solid, force;
+    int rules;
     bool operator==(const TuneKey& o) const {
-        return device == o.device && W == o.W && H == o.H && solid == o.solid && force == o.force;
+        return device == o.device && W == o.W && H == o.H && solid == o.solid && force == o.force &&
+               rules == o.rules;
     }
 };
 struct TuneChoice {
@@ -169,7 +171,7 @@ void effective_settings(const fhp_lattice* h, int* kernel, int* k_block) {
     *k_block = h->k_block;
     if (h->step_kernel != fhp::kStepAuto || h->k_block != 1) return;
     TuneChoice c;
-    if (tuned_choice(TuneKey{h->device, h->g.W, h->g.H, h->has_solid, h->force}, &c)) {
+    if (tuned_choice(TuneKey{h->device, h->g.W, h->g.H, h->has_solid, h->force, h->g.rules}, &c)) {
         *kernel = c.kernel;
         *k_block = c.k;
         return;
@@ -564,8 +566,8 @@ int fhp_get_step_kernel(const fhp_lattice* h) {
 
 int fhp_set_rules(fhp_lattice* h, int32_t rules) {
     if (!h) return fail(nullptr, FHP_EINVAL, "lattice is NULL");
-    if (rules != FHP_RULES_FHP_I && rules != FHP_RULES_FHP_II)
-        return fail(h, FHP_EINVAL, "rule set %d is not FHP_RULES_FHP_I (1) or FHP_RULES_FHP_II (2)", rules);
+    if (rules != FHP_RULES_FHP_I && rules != FHP_RULES_FHP_II && rules != FHP_RULES_FHP_III)
+        return fail(h, FHP_EINVAL, "rule set %d is not FHP_RULES_FHP_I (1), _II (2) or _III (3)", rules);
     h->g.rules = rules;
     return FHP_OK;
 }
@@ -706,7 +708,7 @@ int fhp_autotune(fhp_lattice* h, int32_t trial_steps, int32_t* out_kernel, int32
     // shape (and obstacle / forcing flags) on this device.
     h->step_kernel = fhp::kStepAuto;
     h->k_block = 1;
-    record_tuned(TuneKey{h->device, h->g.W, h->g.H, h->has_solid, h->force}, best);
+    record_tuned(TuneKey{h->device, h->g.W, h->g.H, h->has_solid, h->force, h->g.rules}, best);
     if (out_kernel) *out_kernel = best.kernel;
     if (out_temporal_block) *out_temporal_block = best.k;
     return FHP_OK;

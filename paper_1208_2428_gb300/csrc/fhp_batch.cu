@@ -857,7 +857,7 @@ int fhp_batch_load_obstacle_shapes(fhp_batch* b, int32_t slot, const fhp_shape* 
 int fhp_batch_set_rules(fhp_batch* b, int32_t slot, int32_t rules) {
     Member* m = member(b, slot);
     if (!m || (rules != FHP_RULES_FHP_I && rules != FHP_RULES_FHP_II))
-        return bfail(b, FHP_EINVAL, "invalid slot %d or rule set %d", slot, rules);
+        return bfail(b, FHP_EINVAL, "invalid slot %d or rule set %d (members: FHP-I or FHP-II)", slot, rules);
     m->g.rules = rules;
     return FHP_OK;
 }

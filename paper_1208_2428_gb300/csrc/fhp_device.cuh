@@ -113,6 +113,79 @@ __host__ __device__ __forceinline__ Planes7 scatter(const Planes7 in, uint32_t s
 }
 
 // ---------------------------------------------------------------------------
+// Scattering of 32 nodes at once, FHP-III (collision-saturated): every fluid
+// state that shares its mass and momentum with another state changes, as a
+// per-bit flip mask over disjoint state classes (k = 0..5 below, indices of
+// movers mod 6; "pair p" = movers p and p+3):
+//   zero momentum (every pair full or empty, or a triple): the movers turn
+//     by +60 deg (chi 0) or -60 deg (chi 1), the rest particle stays;
+//   rest + k <-> {k-1, k+1}                    flip rest, k-1, k, k+1
+//   all movers but k+3 <-> rest + {k-1,k,k+1,k+3}   flip rest, k+2, k+3, k+4
+//   momentum c_k, mass 3, chi 0: A = k + pair k+1 -> B = k + pair k+2
+//     -> C = rest + {k-1, k+1} -> A  (chi 1 backwards)
+//   momentum c_k, mass 4, chi 0: D = rest + k + pair k+2 -> E = rest + k +
+//     pair k+1 -> F = {k-1, k+1} + pair k -> D  (chi 1 backwards)
+// Solid nodes reverse every mover (i <-> i+3) and keep the rest particle.
+// ---------------------------------------------------------------------------
+__host__ __device__ __forceinline__ Planes7 scatter_saturated(const Planes7 in, uint32_t solid, uint32_t chi) {
+    const uint32_t a[6] = {in.m0, in.m1, in.m2, in.m3, in.m4, in.m5};
+    const uint32_t r = in.rest, nr = ~in.rest, nchi = ~chi;
+    uint32_t full[3], empty[3], lone[6];
+#pragma unroll
+    for (int p = 0; p < 3; ++p) {
+        full[p] = a[p] & a[p + 3];
+        empty[p] = ~(a[p] | a[p + 3]);
+    }
+#pragma unroll
+    for (int i = 0; i < 6; ++i) lone[i] = a[i] & ~a[(i + 3) % 6];
+    const uint32_t triple = (lone[0] & lone[2] & lone[4]) | (lone[1] & lone[3] & lone[5]);
+    const uint32_t zero = ((full[0] | empty[0]) & (full[1] | empty[1]) & (full[2] | empty[2])) | triple;
+
+    uint32_t f[6], fr = 0u;
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+        f[i] = zero & (a[i] ^ ((chi & a[(i + 1) % 6]) | (nchi & a[(i + 5) % 6])));
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        const int km2 = (k + 4) % 6, km1 = (k + 5) % 6, kp1 = (k + 1) % 6, kp2 = (k + 2) % 6, kp3 = (k + 3) % 6,
+                  kp4 = (k + 4) % 6;
+        const uint32_t pk = full[k % 3], p1 = full[(k + 1) % 3], p2 = full[(k + 2) % 3];
+        const uint32_t x = p1 & lone[k] & empty[(k + 2) % 3];       // k + pair k+1
+        const uint32_t y = p2 & lone[k] & empty[(k + 1) % 3];       // k + pair k+2
+        const uint32_t side = lone[km1] & lone[kp1];                // movers k-1 and k+1
+        const uint32_t A = x & nr, E = x & r, B = y & nr, D = y & r;
+        const uint32_t C = r & side & empty[k % 3], F = nr & side & pk;
+        // two-state classes
+        const uint32_t q = (r & lone[k] & empty[(k + 1) % 3] & empty[(k + 2) % 3]) | (nr & side & empty[k % 3]);
+        const uint32_t s5 = (nr & p1 & p2 & lone[k]) | (r & pk & side);
+        // three-state cycles
+        const uint32_t ab = (nchi & A) | (chi & B) | (nchi & D) | (chi & E);   // flip k-2, k-1, k+1, k+2
+        const uint32_t bc = (nchi & B) | (chi & C);                           // flip k, k+1, k+2, rest
+        const uint32_t ca = (nchi & C) | (chi & A);                           // flip k-2, k-1, k, rest
+        const uint32_t ef = (nchi & E) | (chi & F);                           // flip k-2, k-1, k+3, rest
+        const uint32_t fd = (nchi & F) | (chi & D);                           // flip k+1, k+2, k+3, rest
+        f[km1] |= q | ab | ca | ef;
+        f[k] |= q | bc | ca;
+        f[kp1] |= q | ab | bc | fd;
+        f[kp2] |= s5 | ab | bc | fd;
+        f[kp3] |= s5 | ef | fd;
+        f[kp4] |= s5;
+        f[km2] |= ab | ca | ef;
+        fr |= q | s5 | bc | ca | ef | fd;
+    }
+    Planes7 out;
+    const uint32_t fl = ~solid;
+    out.m0 = (solid & a[3]) | (fl & (a[0] ^ f[0]));
+    out.m1 = (solid & a[4]) | (fl & (a[1] ^ f[1]));
+    out.m2 = (solid & a[5]) | (fl & (a[2] ^ f[2]));
+    out.m3 = (solid & a[0]) | (fl & (a[3] ^ f[3]));
+    out.m4 = (solid & a[1]) | (fl & (a[4] ^ f[4]));
+    out.m5 = (solid & a[2]) | (fl & (a[5] ^ f[5]));
+    out.rest = r ^ (fl & fr);
+    return out;
+}
+
+// ---------------------------------------------------------------------------
 // Forcing (ForcingTable: Q_g, g = 0..32, in units of 2^-32 -- a uniform
 // u < Q_g means "one of the next g candidates is forced").
 // ---------------------------------------------------------------------------

@@ -34,7 +34,7 @@ struct Geometry {
     int Pq = 0;         // row pitch in words (multiple of 4)
     size_t plane_words = 0;  // H * Pq
     int row_base = 0;   // lattice row of array row 0 (a strip of a larger lattice; even)
-    int rules = 2;      // collision rule set: 2 = FHP-II, 1 = FHP-I
+    int rules = 2;      // collision rule set: 2 = FHP-II, 1 = FHP-I, 3 = FHP-III (direct kernel only)
 };
 
 // Mask that enables the rest-particle rules of the bit-sliced scattering.

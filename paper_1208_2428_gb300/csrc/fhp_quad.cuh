@@ -47,7 +47,9 @@ struct StepVar {
 // Scattering, bounce-back and forcing of one quad (global quad index q of
 // row y at step v.t) whose movers have already been pulled (n0..n5), with
 // rest plane i6 and solid plane sd; the seven result planes go to o[0..6].
-template <bool SOLID, bool FORCE>
+// SAT selects the FHP-III (collision-saturated) rule set at compile time;
+// otherwise FHP-II or FHP-I by the lattice's rest-particle mask.
+template <bool SOLID, bool FORCE, bool SAT = false>
 __device__ __forceinline__ void collide_quad(const StepArgs& a, const StepVar& v, int q, int y, uint4 n0, uint4 n1,
                                              uint4 n2, uint4 n3, uint4 n4, uint4 n5, uint4 i6, uint4 sd,
                                              uint4 (&o)[7]) {
@@ -58,7 +60,8 @@ __device__ __forceinline__ void collide_quad(const StepArgs& a, const StepVar& v
 #define FHP_WORD(J, C, RR)                                                                      \
     {                                                                                           \
         Planes7 in{n0.C, n1.C, n2.C, n3.C, n4.C, n5.C, i6.C};                                   \
-        Planes7 out = scatter(in, SOLID ? sd.C : 0u, chi.C, RR);                                \
+        Planes7 out = SAT ? scatter_saturated(in, SOLID ? sd.C : 0u, chi.C)                      \
+                          : scatter(in, SOLID ? sd.C : 0u, chi.C, RR);                          \
         if (FORCE) {                                                                            \
             const uint32_t cand = (SOLID ? ~sd.C : 0xFFFFFFFFu) & out.m5 & ~out.m2;             \
             const uint32_t u = gate.C;                                                          \
@@ -77,7 +80,7 @@ __device__ __forceinline__ void collide_quad(const StepArgs& a, const StepVar& v
     }
     // The rule set is uniform over a launch (and a batch tile): one branch
     // selects code in which the rest-particle mask is a constant.
-    if (a.rest_rules != 0u) {
+    if (SAT || a.rest_rules != 0u) {
         FHP_WORD(0, x, 0xFFFFFFFFu)
         FHP_WORD(1, y, 0xFFFFFFFFu)
         FHP_WORD(2, z, 0xFFFFFFFFu)
@@ -111,12 +114,12 @@ __device__ __forceinline__ void store_quad(const StepArgs& a, uint32_t* dst, int
 }
 
 // Collide and store one quad.
-template <bool SOLID, bool FORCE, bool RAGGED>
+template <bool SOLID, bool FORCE, bool RAGGED, bool SAT = false>
 __device__ __forceinline__ void finish_quad(const StepArgs& a, const StepVar& v, int q, int y, int m, uint4 n0,
                                             uint4 n1, uint4 n2, uint4 n3, uint4 n4, uint4 n5, uint4 i6,
                                             uint4 sd, bool active) {
     uint4 o[7];
-    collide_quad<SOLID, FORCE>(a, v, q, y, n0, n1, n2, n3, n4, n5, i6, sd, o);
+    collide_quad<SOLID, FORCE, SAT>(a, v, q, y, n0, n1, n2, n3, n4, n5, i6, sd, o);
     if (active) store_quad<RAGGED>(a, v.dst, q, y, m, o);
 }
 

@@ -315,7 +315,7 @@ __device__ __forceinline__ uint32_t right_word(uint4 v, uint32_t fallback, const
     return L.glob_right ? fallback : right;
 }
 
-template <bool SOLID, bool FORCE, bool RAGGED, bool ODD>
+template <bool SOLID, bool FORCE, bool RAGGED, bool ODD, bool SAT>
 __device__ __forceinline__ void direct_quad(const StepArgs& a, const Lane& L) {
     const size_t pw = a.plane_words;
     const int y = L.y;
@@ -359,14 +359,16 @@ __device__ __forceinline__ void direct_quad(const StepArgs& a, const Lane& L) {
         n1 = i1;
     }
     const StepVar v{a.dst, a.t_lo, a.t_hi};
-    finish_quad<SOLID, FORCE, RAGGED>(a, v, L.q, y, m, n0, n1, n2, n3, n4, n5, i6, sd, L.active);
+    finish_quad<SOLID, FORCE, RAGGED, SAT>(a, v, L.q, y, m, n0, n1, n2, n3, n4, n5, i6, sd, L.active);
 }
 
-template <bool SOLID, bool FORCE, bool RAGGED>
-__global__ void __launch_bounds__(kBlock, 4) fhp_step_direct_kernel(const StepArgs a) {
+// SAT: the FHP-III rule set (the only kernel that carries it; its larger
+// scattering network gets twice the registers).
+template <bool SOLID, bool FORCE, bool RAGGED, bool SAT>
+__global__ void __launch_bounds__(kBlock, SAT ? 2 : 4) fhp_step_direct_kernel(const StepArgs a) {
     const Lane L = map_lane(a);
-    if (L.y & 1) direct_quad<SOLID, FORCE, RAGGED, true>(a, L);
-    else direct_quad<SOLID, FORCE, RAGGED, false>(a, L);
+    if (L.y & 1) direct_quad<SOLID, FORCE, RAGGED, true, SAT>(a, L);
+    else direct_quad<SOLID, FORCE, RAGGED, false, SAT>(a, L);
 }
 
 __global__ void philox_kernel(const uint32_t* __restrict__ ctr, const uint32_t* __restrict__ key,
@@ -485,11 +487,16 @@ cudaError_t launch_tma(const StepArgs& a, const TileArgs& ta, size_t smem, bool 
 }
 
 template <bool SOLID, bool FORCE>
-cudaError_t launch_direct(const StepArgs& a, bool ragged, long long warps, cudaStream_t s) {
+cudaError_t launch_direct(const StepArgs& a, bool ragged, bool sat, long long warps, cudaStream_t s) {
     const long long threads = warps * 32;
     const unsigned grid = (unsigned)((threads + kBlock - 1) / kBlock);
-    if (ragged) fhp_step_direct_kernel<SOLID, FORCE, true><<<grid, kBlock, 0, s>>>(a);
-    else fhp_step_direct_kernel<SOLID, FORCE, false><<<grid, kBlock, 0, s>>>(a);
+    if (sat) {
+        if (ragged) fhp_step_direct_kernel<SOLID, FORCE, true, true><<<grid, kBlock, 0, s>>>(a);
+        else fhp_step_direct_kernel<SOLID, FORCE, false, true><<<grid, kBlock, 0, s>>>(a);
+    } else {
+        if (ragged) fhp_step_direct_kernel<SOLID, FORCE, true, false><<<grid, kBlock, 0, s>>>(a);
+        else fhp_step_direct_kernel<SOLID, FORCE, false, false><<<grid, kBlock, 0, s>>>(a);
+    }
     return cudaGetLastError();
 }
 
@@ -525,7 +532,7 @@ Geometry make_geometry(int W, int H) {
 
 int resolved_step_kernel(const Geometry& g, bool has_solid, int requested) {
     const int R = tile_rows(g, has_solid);
-    if (R == 0 || requested == kStepDirect) return kStepDirect;
+    if (R == 0 || requested == kStepDirect || g.rules == 3) return kStepDirect;   // FHP-III: direct kernel only
     if (requested == kStepRing || requested == kStepRun) return requested;
     int dev = 0, sms = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return kStepDirect;
@@ -642,10 +649,10 @@ cudaError_t launch_step(const Geometry& g, const uint32_t* src, uint32_t* dst,
         warps = 2LL * a.groups_per_parity;
     }
     if (has_solid)
-        return force ? launch_direct<true, true>(a, ragged, warps, stream)
-                     : launch_direct<true, false>(a, ragged, warps, stream);
-    return force ? launch_direct<false, true>(a, ragged, warps, stream)
-                 : launch_direct<false, false>(a, ragged, warps, stream);
+        return force ? launch_direct<true, true>(a, ragged, g.rules == 3, warps, stream)
+                     : launch_direct<true, false>(a, ragged, g.rules == 3, warps, stream);
+    return force ? launch_direct<false, true>(a, ragged, g.rules == 3, warps, stream)
+                 : launch_direct<false, false>(a, ragged, g.rules == 3, warps, stream);
 }
 
 }  // namespace fhp

@@ -360,7 +360,60 @@ def test_fhp1_batch_member(fhp_mod, oracle_mod):
             assert np.array_equal(b.get_state(k), want), r
     with fhp_mod.Lattice(W, H) as lat:
         with pytest.raises(fhp_mod.FhpError):
-            lat.set_rules(3)
+            lat.set_rules(4)
+
+
+@pytest.mark.parametrize("W,H,p,obstacle,kernel,k", [
+    (1024, 130, 0.01, "points", 0, 1), (4096, 256, 0.0, "cylinder", 3, 1), (96, 8, 0.05, "walls", 4, 2),
+    (160, 66, 0.0, "none", 2, 4), (4128, 4, 0.2, "points", 0, 1)])
+def test_fhp3_rules_parity(fhp_mod, oracle_mod, W, H, p, obstacle, kernel, k):
+    """FHP-III (collision-saturated) runs on the direct kernel whatever the
+    kernel and temporal-block settings; bit-exact with the oracle's FHP-III
+    run on walls, points, a cylinder, forcing and ragged rows."""
+    seed = 999 + W + H
+    job = workloads.Lattice("fhp3", W, H, 0.35, seed, p, 0, obstacle=obstacle, point_frac=0.02)
+    s0 = job.initial_state()
+    want, _ = oracle_mod.run(s0, seed, 3, 21, p, rules=3)
+    with fhp_mod.Lattice(W, H, seed=seed, forcing_p=p, step_kernel=kernel) as lat:
+        lat.set_rules(3)
+        assert lat.rules == 3 and lat.step_kernel == 1 and lat.temporal_block == 1
+        lat.set_temporal_block(k)
+        assert lat.temporal_block == 1
+        lat.set_state(s0)
+        lat.set_time(3)
+        lat.step(21)
+        got = lat.get_state()
+        assert_same(got, want, f"FHP-III {W}x{H}")
+        # back to FHP-II for the next steps: the multi-step kernels again
+        lat.set_rules(2)
+        lat.step(5)
+        more, _ = oracle_mod.run(want, seed, 24, 5, p, rules=2)
+        assert_same(lat.get_state(), more, "FHP-II after FHP-III")
+    other, _ = oracle_mod.run(s0, seed, 3, 21, p, rules=2)
+    assert not np.array_equal(other, want)
+
+
+def test_fhp3_autotune_and_batch(fhp_mod, oracle_mod):
+    """An FHP-III lattice tunes to the direct kernel without touching the
+    choice recorded for FHP-II lattices of its shape; batches refuse FHP-III."""
+    W, H = 2048, 512
+    s0 = workloads.bernoulli_lattice(W, H, 0.3, 12)
+    with fhp_mod.Lattice(W, H, seed=12) as a:
+        a.set_state(s0)
+        kern2, k2 = a.autotune(16)
+        a.set_rules(3)
+        kern3, k3 = a.autotune(16)
+        assert (kern3, k3) == (1, 1)
+        assert a.step_kernel == 1
+        a.step(7)
+        want, _ = oracle_mod.run(s0, 12, 0, 7, 0.0, rules=3)
+        assert_same(a.get_state(), want, "FHP-III after autotune")
+    with fhp_mod.Lattice(W, H, seed=12) as b:
+        assert (b.step_kernel, b.temporal_block) == (kern2, k2)
+    with fhp_mod.Batch(fhp_mod.Batch.lattice_bytes(W, H) + (16 << 20)) as bt:
+        slot = bt.add(W, H, 1, 0.0)
+        with pytest.raises(fhp_mod.FhpError):
+            bt.set_rules(slot, 3)
 
 
 @pytest.mark.parametrize("W,H,steps", [(4096, 1024, 1), (4096, 1024, 2), (4096, 1024, 37), (2048, 512, 40),

@@ -24,10 +24,12 @@ def host_scatter(tmp_path_factory):
     lib.host_scatter_words.argtypes = [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
                                        ctypes.c_void_p]
     lib.host_scatter_words.restype = None
+    lib.host_scatter_saturated_words.argtypes = [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_void_p]
+    lib.host_scatter_saturated_words.restype = None
     return lib
 
 
-@pytest.mark.parametrize("rules,mask", [(2, 0xFFFFFFFF), (1, 0)])
+@pytest.mark.parametrize("rules,mask", [(2, 0xFFFFFFFF), (1, 0), (3, None)])
 def test_bitsliced_scatter_equals_table(host_scatter, oracle_mod, rules, mask):
     tables = [oracle_mod.table(0, rules=rules), oracle_mod.table(1, rules=rules)]
     states = np.arange(256, dtype=np.uint32)
@@ -39,7 +41,10 @@ def test_bitsliced_scatter_equals_table(host_scatter, oracle_mod, rules, mask):
                                for k in range(7)], dtype=np.uint32)
             solid = np.uint32(int(((nodes >> 7) & 1) @ (1 << np.arange(32, dtype=np.uint64))))
             out = np.zeros(7, dtype=np.uint32)
-            host_scatter.host_scatter_words(planes.ctypes.data, int(solid), chi_pattern, mask, out.ctypes.data)
+            if rules == 3:
+                host_scatter.host_scatter_saturated_words(planes.ctypes.data, int(solid), chi_pattern, out.ctypes.data)
+            else:
+                host_scatter.host_scatter_words(planes.ctypes.data, int(solid), chi_pattern, mask, out.ctypes.data)
             for j in range(32):
                 b = int(nodes[j])
                 chi = (chi_pattern >> j) & 1
