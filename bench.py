@@ -65,6 +65,8 @@ def parse_args():
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="target CPU time of the oracle baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-k-sweep", action="store_true",
+                    help="skip the temporal-block comparison (k = 1, 2, 4, 8) of the cylinder line")
     ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
 
@@ -576,6 +578,10 @@ def run_gpu(args):
                        "one_lattice_at_a_time": serving_cmp["one_lattice_at_a_time"],
                        "peak_resident": serving_cmp["peak_resident"]}
 
+    k_sweep = None
+    if rank == 0 and not args.no_k_sweep and args.workload == "cylinder":
+        k_sweep = temporal_block_sweep(job, s0, seed, dev, stream, nsteps, peak)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(job, s0, args.cpu_seconds)
@@ -605,6 +611,7 @@ def run_gpu(args):
             "e2e": e2e,
             "batched_vs_per_lattice": batch_cmp,
             "serving_reduced": serving_cmp,
+            "temporal_blocks": k_sweep,
             "gpu_launches": launches,
             "clocks": clocks,
         }
@@ -613,6 +620,42 @@ def run_gpu(args):
     if dist:
         dist.destroy_process_group()
     return 0
+
+
+def temporal_block_sweep(job, s0, seed, dev, stream, nsteps, peak):
+    """One call of `nsteps` lattice steps from the same state for temporal
+    blocks k = 1, 2, 4, 8 (k = 1: the automatic single-step choice): GSUPS,
+    the HBM fraction of the algorithmic bytes (a blocked pass reads and writes
+    the state once per k steps) and whether the final states are identical."""
+    import numpy as np
+    import torch
+    from paper_1208_2428_gb300 import Lattice
+    bytes_per_node = (14 + (1 if (s0 & 0x80).any() else 0)) / 8.0
+    out, ref = {}, None
+    for k in (1, 2, 4, 8):
+        with Lattice(job.W, job.H, seed=seed, forcing_p=job.p, device=dev, stream=stream) as lat:
+            lat.set_step_kernel(0)
+            lat.set_temporal_block(k)
+            used_k = lat.temporal_block
+            lat.set_state(s0)
+            lat.step(64)
+            lat.set_state(s0)
+            lat.set_time(0)
+            torch.cuda.synchronize(dev)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            lat.step(nsteps)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            ms = e0.elapsed_time(e1)
+            final = lat.get_state()
+        if ref is None:
+            ref = final
+        gsups = job.W * job.H * nsteps / (ms / 1e3) / 1e9
+        out[f"k{k}"] = {"temporal_block": used_k, "gsups": gsups, "ms": ms,
+                        "hbm_frac": gsups * 1e9 * bytes_per_node / used_k / (peak * 1e9),
+                        "same_final_state_as_k1": bool(np.array_equal(final, ref))}
+    return out
 
 
 def main():
