@@ -158,8 +158,11 @@ FHP_API int fhp_set_forcing(fhp_lattice* lattice, double p);
  * in shared memory and apply k steps there before writing the tile back, so
  * HBM is read and written once per k steps; leftover steps (n mod k) and
  * lattices the blocked kernel does not support (W not a multiple of 128,
- * fewer than 512 nodes per row, or H < 2k + 2) use the single-step kernels.
- * Results are identical for every value.  Default 1. */
+ * fewer than 512 nodes per row, H < 2k + 2, or the FHP-III rule set) use the
+ * single-step kernels.  With step kernel 4 (resident) the value is instead
+ * the number of steps between exchanges of strip rows: 2 selects the
+ * two-ghost-row variant where every strip holds at least 4 rows, other values
+ * the one-row exchange.  Results are identical for every value.  Default 1. */
 FHP_API int fhp_set_temporal_block(fhp_lattice* lattice, int32_t k);
 
 /* Obstacles generated on the device from simple shapes (the walls and
@@ -223,15 +226,18 @@ FHP_API int fhp_get_rows_device(fhp_lattice* lattice, int32_t y0, int32_t n, uin
 FHP_API int fhp_set_rows_device(fhp_lattice* lattice, int32_t y0, int32_t n, const uint32_t* device_words);
 
 /* Temporal block fhp_step will use (1 if blocking is off or unsupported for
- * this lattice), or -1 for a NULL lattice. */
+ * this lattice; for the resident kernel the exchange interval, 1 or 2), or
+ * -1 for a NULL lattice. */
 FHP_API int fhp_get_temporal_block(const fhp_lattice* lattice);
 
 /* Autotuner.  Times every step configuration that applies to this lattice --
- * direct, ring and multi-step kernels, and temporal blocks k = 2, 4, 8 --
+ * direct, ring, multi-step and resident kernels (the resident one with
+ * exchanges every step and every second step), and temporal blocks
+ * k = 2, 4, 8 --
  * over trial_steps steps each (a multiple of 8 in [8, 4096]; each candidate
  * runs once untimed, then timed with CUDA events on the lattice's stream) and
- * records the fastest for this device, lattice shape, and whether the
- * lattice has obstacles and forcing.  From then on every lattice of that
+ * records the fastest for this device, lattice shape, rule set, and whether
+ * the lattice has obstacles and forcing.  From then on every lattice of that
  * description whose settings are automatic (kernel 0, temporal block 1) runs
  * the recorded configuration.  The state and the step counter are those of
  * the call on return (the trials run from a saved copy of the state, which
@@ -251,8 +257,10 @@ FHP_API int fhp_autotune(fhp_lattice* lattice, int32_t trial_steps, int32_t* out
  * running all steps of an fhp_step call in one cooperative launch, each tile
  * waiting only for the three tiles of the previous step it reads).  2 and 3
  * fall back to 1 when a row does not fit a stage; automatic picks 1 for
- * lattices of fewer than 8 tiles, 3 up to 24 tiles per SM and 2 above.  Results are identical for
- * every choice.  While the kernel is automatic and the temporal block 1, a
+ * lattices of fewer than 8 tiles, 4 (with exchanges every second step where
+ * the strips allow it) for lattices of fewer than 2 tiles per SM whose strips
+ * fit, 3 up to 24 tiles per SM and 2 above; FHP-III lattices always run 1.
+ * Results are identical for every choice.  While the kernel is automatic and the temporal block 1, a
  * configuration recorded by fhp_autotune for the lattice's description takes
  * precedence. */
 FHP_API int fhp_set_step_kernel(fhp_lattice* lattice, int32_t kind);
