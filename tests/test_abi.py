@@ -36,6 +36,13 @@ def test_required_bytes_and_validation_without_gpu(lib):
     assert planes <= n <= planes + 16384 * 4096 + 4 * 4096 + 4096
     # ragged rows are padded to whole 16-byte quads
     assert lib.fhp_required_bytes(96, 2) >= 15 * 2 * 16 + 96 * 2
+    # the staging area also holds the two-ghost-row exchange (144 bytes per row
+    # quad for each of up to min(H/4, 256) strips) where that exceeds W*H
+    for W, H in ((4096, 1024), (512, 608), (4128, 640), (16384, 4096)):
+        Pq = 4 * ((W // 32 + 3) // 4)
+        staging = max(W * H, 144 * min(H // 4, 256) * Pq)
+        n = lib.fhp_required_bytes(W, H)
+        assert 15 * H * Pq * 4 + staging <= n <= 15 * H * Pq * 4 + staging + 4 * H + 4096, (W, H)
     out = ctypes.c_void_p(123)
     rc = lib.fhp_create(ctypes.byref(out), None)
     assert rc == fhp.FHP_EINVAL and out.value is None
