@@ -12,14 +12,15 @@
 
 namespace fhp {
 
-
 constexpr int kResThreads = 384;   // 12 warps: 3 per SM sub-partition at <= 168 registers
+                                   // (both kernels use at most 160: no spills)
 constexpr int kResSmemLimit = 220 * 1024;
 
 struct ResArgs {
     uint32_t* buf0;        // state at t0; also the result when nsteps is even
     uint32_t* buf1;        // the result when nsteps is odd
-    uint32_t* halo;        // exchange rows: [2 parities][G][2 sides][2 planes][Pq] words
+    uint32_t* halo;        // exchange rows: [2 parities][G][2 sides][row planes][Pq] words (2 row
+                           // planes per side for the one-row exchange, 9 for two ghost rows)
     unsigned int* flags;   // [G] step counters, zero at launch
     int nsteps;
     unsigned long long t0;
