@@ -465,17 +465,27 @@ def run_gpu(args):
         if B:
             lat.coarse_grain_into(B, counts, rho, ux, uy)
 
+    # Coarse-grained fields every `every` lattice steps where the workload asks
+    # for them (the channel: every 1,000 of its 10,000 steps), else once at the
+    # end of the benchmark step.
+    cg_every = getattr(job, "cg_every", None)
+    every = cg_every if (B and cg_every and nsteps % cg_every == 0) else nsteps
+    chunks = nsteps // every
+
     def bench_step():
-        lat.step(nsteps)
-        coarse()
+        for _ in range(chunks):
+            lat.step(every)
+            coarse()
 
     for _ in range(args.warmup):
         bench_step()
     torch.cuda.synchronize(dev)
 
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    mids = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    # around each fhp_step call of the timed region (one per chunk)
+    step_ev = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                for _ in range(chunks)] for _ in range(args.steps)]
     gpu_index = int(os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[0]) \
         if os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")[0].isdigit() else local
     sampler = ClockSampler(gpu_index)
@@ -488,9 +498,11 @@ def run_gpu(args):
     for i in range(args.steps):
         flush.fill_(i & 0xFF)                       # L2 flush between timed steps
         starts[i].record(stream)
-        lat.step(nsteps)
-        mids[i].record(stream)
-        coarse()
+        for c in range(chunks):
+            step_ev[i][c][0].record(stream)
+            lat.step(every)
+            step_ev[i][c][1].record(stream)
+            coarse()
         ends[i].record(stream)
     torch.cuda.synchronize(dev)
     if dist:
@@ -508,7 +520,7 @@ def run_gpu(args):
         kernel_name = f"fhp_block_kernel (k={k_block})"
     k_pass = 1 if resident else k_block
     total_ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
-    step_kernel_ms = sum(s.elapsed_time(m) for s, m in zip(starts, mids))
+    step_kernel_ms = sum(a.elapsed_time(b) for evs in step_ev for a, b in evs)
     if dist:
         t = torch.tensor([total_ms, step_kernel_ms], dtype=torch.float64, device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -520,7 +532,7 @@ def run_gpu(args):
     # Step-kernel launches in the timed region: one per lattice step for the
     # single-step kernels, one per fhp_step call (chunks of 2^24 steps) for
     # the multi-step kernel.
-    cg_launches = args.steps if B else 0
+    cg_launches = args.steps * chunks if B else 0
     step_launches = max(1, launches - cg_launches)
     steps_per_launch = nsteps * args.steps / step_launches
     launch_s = step_kernel_ms / 1e3 / step_launches
@@ -543,10 +555,11 @@ def run_gpu(args):
         e2e_steps = max(3, min(args.steps, 10))
         def e2e_step():
             lat.set_state(host_state)
-            lat.step(nsteps)
-            if B:
-                lat.coarse_grain_host_into(B, h_counts, h_rho, h_ux, h_uy)
-            else:
+            for _ in range(chunks):
+                lat.step(every)
+                if B:
+                    lat.coarse_grain_host_into(B, h_counts, h_rho, h_ux, h_uy)
+            if not B:
                 lat.synchronize()
         e2e_step()
         if dist:
@@ -563,7 +576,8 @@ def run_gpu(args):
             e2e_s = float(t[0])
         e2e = {"value": world * nodes * nsteps * e2e_steps / e2e_s / 1e9, "unit": UNIT,
                "h2d_bytes_per_step": int(s0.nbytes),
-               "d2h_bytes_per_step": int(h_counts.nbytes + h_rho.nbytes + h_ux.nbytes + h_uy.nbytes) if B else 0,
+               "d2h_bytes_per_step": chunks * int(h_counts.nbytes + h_rho.nbytes + h_ux.nbytes + h_uy.nbytes)
+               if B else 0,
                "steps": e2e_steps}
 
     batch_cmp = None
@@ -593,7 +607,7 @@ def run_gpu(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "u32 (bit-planes, boolean/integer)",
             "data": "synthetic (seeded Bernoulli lattice, index-coordinate cylinder)",
             "config": {"workload": job.name, "W": job.W, "H": job.H, "lattice_steps_per_step": nsteps,
-                       "coarse_grain_block": B, "forcing_p": job.p, "density": job.density,
+                       "coarse_grain_block": B, "coarse_grain_every": every if B else None, "forcing_p": job.p, "density": job.density,
                        "seed": job.seed, "temporal_block": k_block,
                        "autotuned": {"kernel": tuned[0], "temporal_block": tuned[1]} if tuned else None,
                        "step_kernel": kernel_name,
