@@ -320,7 +320,7 @@ def test_device_philox_matches_oracle(fhp_mod, oracle_mod):
         assert np.array_equal(got[i], oracle_mod.philox4x32_10(ctr[i], key[i])), i
 
 
-@pytest.mark.parametrize("kernel,k", [(1, 1), (2, 1), (3, 1), (0, 2), (0, 4)])
+@pytest.mark.parametrize("kernel,k", [(1, 1), (2, 1), (3, 1), (0, 2), (0, 4), (4, 1)])
 def test_fhp1_rules_parity(fhp_mod, oracle_mod, kernel, k):
     """FHP-I (no rest-particle collisions) on every kernel, with walls,
     points and forcing, against the oracle's FHP-I run."""
@@ -472,3 +472,39 @@ def test_resident_ghost_falls_back_to_one_row(fhp_mod, oracle_mod):
         lat.set_state(s0)
         lat.step(6)
         assert_same(lat.get_state(), want, "resident fallback")
+
+
+def test_fhp1_resident_ghost_rows(fhp_mod, oracle_mod):
+    """FHP-I through the two-ghost-row resident kernel (strips of 6-7 rows)."""
+    W, H, seed, p = 4096, 1024, 515, 0.01
+    s0 = workloads.bernoulli_lattice(W, H, 0.3, seed, workloads.channel_walls(W, H))
+    want, _ = oracle_mod.run(s0, seed, 1, 15, p, rules=1)
+    with fhp_mod.Lattice(W, H, seed=seed, forcing_p=p, step_kernel=4) as lat:
+        lat.set_rules(1)
+        lat.set_temporal_block(2)
+        assert lat.step_kernel == 4 and lat.temporal_block == 2
+        lat.set_state(s0)
+        lat.set_time(1)
+        lat.step(15)
+        assert_same(lat.get_state(), want, "FHP-I resident ghost")
+
+
+def test_fhp3_row_strips(fhp_mod, oracle_mod):
+    """FHP-III on row strips of one lattice (row offsets key the random words;
+    ghost rows exchanged through device buffers) equals the whole lattice."""
+    from paper_1208_2428_gb300.strips import DeviceStrip, LocalExchange, StripDomain, StripPlan
+    W, H, seed, p, steps = 512, 96, 4242, 2e-3, 11
+    s0 = workloads.Lattice("s3", W, H, 0.3, seed, p, 0, obstacle="cylinder").initial_state()
+    plan = StripPlan(W, H, 3, 4)
+    strips = [DeviceStrip(plan, r, seed, p) for r in range(3)]
+    try:
+        for st in strips:
+            st.set_from_global(s0)
+            st.lattice.set_rules(3)
+        StripDomain(plan, strips, LocalExchange()).step(steps)
+        got = np.concatenate([st.owned_state() for st in strips])
+    finally:
+        for st in strips:
+            st.close()
+    want, _ = oracle_mod.run(s0, seed, 0, steps, p, rules=3)
+    assert_same(got, want, "FHP-III strips")
