@@ -61,6 +61,10 @@ def parse_args():
                     help="keep the automatic kernel choice instead of timing the configurations first")
     ap.add_argument("--step-kernel", type=int, default=0,
                     help="0 auto, 1 direct, 2 bulk-copy ring, 3 multi-step ring")
+    ap.add_argument("--rules", type=int, default=2, choices=[1, 2, 3],
+                    help="collision rule set: 2 FHP-II (default), 1 FHP-I, 3 FHP-III")
+    ap.add_argument("--no-rules-compare", action="store_true",
+                    help="skip the FHP-I / FHP-III throughput comparison of the cylinder line")
     ap.add_argument("--cg-block", type=int, default=32)
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="target CPU time of the oracle baseline sample")
@@ -188,9 +192,34 @@ def dist_setup():
     return world, rank, local
 
 
+def cpu_model() -> str:
+    """Host CPU model (lscpu's "Model name", else /proc/cpuinfo) and thread count."""
+    name = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                name = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if not name:
+        try:
+            with open("/proc/cpuinfo") as f:
+                for line in f:
+                    if line.lower().startswith(("model name", "cpu part")):
+                        name = line.split(":", 1)[1].strip()
+                        break
+        except Exception:
+            pass
+    return f"{name or 'unknown'} ({os.cpu_count()} logical CPUs, {os.uname().machine})"
+
+
 def cpu_baseline(job, s0, target_seconds: float):
-    """Time the CPU oracle (as it stands) on a bounded sample: whole-lattice
-    steps of the benchmark's workload, as many as fit ~target_seconds."""
+    """Time the CPU oracle (as it stands) on bounded samples of the benchmark's
+    workload: whole-lattice steps, as many as fit ~target_seconds, on all host
+    cores (OpenMP row strips, the paper's threaded "Pth" analogue) and on one
+    thread (its "seq" analogue)."""
     import oracle
     oracle.build()
     cores = oracle.max_threads()
@@ -201,9 +230,21 @@ def cpu_baseline(job, s0, target_seconds: float):
     t0 = time.perf_counter()
     oracle.run(s0, job.seed, 1, n, job.p)
     dt = time.perf_counter() - t0
+    single = None
+    try:
+        oracle.set_threads(1)
+        t0 = time.perf_counter()
+        oracle.run(s0, job.seed, 1, 1, job.p)
+        dt1 = time.perf_counter() - t0
+        single = {"value": job.W * job.H / dt1 / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+                  "sample": f"1 whole-lattice time step of the {job.W}x{job.H} workload "
+                            f"({job.W * job.H:.3g} site updates, {dt1:.1f} s, one thread)"}
+    finally:
+        oracle.set_threads(cores)
     return {"value": job.W * job.H * n / dt / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{n} whole-lattice time steps of the {job.W}x{job.H} workload "
-                      f"({job.W * job.H * n:.3g} site updates, {dt:.1f} s, OpenMP row strips)"}
+                      f"({job.W * job.H * n:.3g} site updates, {dt:.1f} s, OpenMP row strips)",
+            "one_thread": single, "cpu_model": cpu_model()}
 
 
 def batched_vs_per_lattice(dev, stream, count: int, steps: int, per_steps: int, repeats: int = 1):
@@ -414,7 +455,8 @@ def run_reference(args):
                    "forcing_p": job.p, "density": job.density, "seed": job.seed,
                    "l2": "n/a (CPU)"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                         "sample": f"each step: {per_step} whole-lattice time steps of {job.W}x{job.H}"},
+                         "sample": f"each step: {per_step} whole-lattice time steps of {job.W}x{job.H}",
+                         "cpu_model": cpu_model()},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -448,6 +490,7 @@ def run_gpu(args):
     stream = torch.cuda.current_stream(dev)
     lat = Lattice(job.W, job.H, seed=seed, forcing_p=job.p, device=dev, stream=stream)
     lat.set_state(s0)
+    lat.set_rules(args.rules)
     lat.set_temporal_block(args.temporal_block)
     lat.set_step_kernel(args.step_kernel)
     tuned = None
@@ -595,6 +638,9 @@ def run_gpu(args):
     k_sweep = None
     if rank == 0 and not args.no_k_sweep and args.workload == "cylinder":
         k_sweep = temporal_block_sweep(job, s0, seed, dev, stream, nsteps, peak)
+    rules_cmp = None
+    if rank == 0 and not args.no_rules_compare and args.workload == "cylinder" and args.rules == 2:
+        rules_cmp = rule_set_comparison(job, s0, seed, dev, stream, nsteps, peak)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -608,7 +654,7 @@ def run_gpu(args):
             "data": "synthetic (seeded Bernoulli lattice, index-coordinate cylinder)",
             "config": {"workload": job.name, "W": job.W, "H": job.H, "lattice_steps_per_step": nsteps,
                        "coarse_grain_block": B, "coarse_grain_every": every if B else None, "forcing_p": job.p, "density": job.density,
-                       "seed": job.seed, "temporal_block": k_block,
+                       "seed": job.seed, "temporal_block": k_block, "rules": f"FHP-{'I' * args.rules}",
                        "autotuned": {"kernel": tuned[0], "temporal_block": tuned[1]} if tuned else None,
                        "step_kernel": kernel_name,
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
@@ -626,6 +672,7 @@ def run_gpu(args):
             "batched_vs_per_lattice": batch_cmp,
             "serving_reduced": serving_cmp,
             "temporal_blocks": k_sweep,
+            "rule_sets": rules_cmp,
             "gpu_launches": launches,
             "clocks": clocks,
         }
@@ -669,6 +716,38 @@ def temporal_block_sweep(job, s0, seed, dev, stream, nsteps, peak):
         out[f"k{k}"] = {"temporal_block": used_k, "gsups": gsups, "ms": ms,
                         "hbm_frac": gsups * 1e9 * bytes_per_node / used_k / (peak * 1e9),
                         "same_final_state_as_k1": bool(np.array_equal(final, ref))}
+    return out
+
+
+def rule_set_comparison(job, s0, seed, dev, stream, nsteps, peak):
+    """One autotuned call of `nsteps` lattice steps for each collision rule set
+    (FHP-I, FHP-II, FHP-III) from the same state: GSUPS, the kernel the tuner
+    chose and the HBM fraction of the algorithmic bytes."""
+    import torch
+    from paper_1208_2428_gb300 import Lattice
+    bytes_per_node = (14 + (1 if (s0 & 0x80).any() else 0)) / 8.0
+    names = {1: "fhp_step_direct_kernel", 2: "fhp_step_tma_kernel", 3: "fhp_run_kernel",
+             4: "fhp_resident_kernel"}
+    out = {}
+    for rules in (1, 2, 3):
+        with Lattice(job.W, job.H, seed=seed, forcing_p=job.p, device=dev, stream=stream) as lat:
+            lat.set_rules(rules)
+            lat.set_state(s0)
+            kernel, k = lat.autotune(64)
+            lat.set_state(s0)
+            lat.set_time(0)
+            lat.step(16)
+            torch.cuda.synchronize(dev)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            lat.step(nsteps)
+            e1.record(stream)
+            lat.synchronize()
+            ms = e0.elapsed_time(e1)
+        gsups = job.W * job.H * nsteps / (ms / 1e3) / 1e9
+        out[f"FHP-{'I' * rules}"] = {"gsups": gsups, "ms": ms, "kernel": names.get(kernel, str(kernel)),
+                                     "temporal_block": k,
+                                     "hbm_frac": gsups * 1e9 * bytes_per_node / k / (peak * 1e9)}
     return out
 
 

@@ -193,8 +193,9 @@ FHP_API int fhp_load_obstacle_shapes(fhp_lattice* lattice, const fhp_shape* shap
  * states turn their movers by +-60 degrees (chirality), two-state classes
  * swap, and the three-state classes of momentum c_k cycle (chirality sets the
  * direction); it keeps every FHP-II collision.  FHP-III lattices step with
- * the direct kernel only (the step-kernel and temporal-block settings are
- * ignored) and cannot be batch members.  Takes effect from the next step.
+ * the direct, bulk-copy ring and multi-step ring kernels (step kernels 1-3;
+ * the resident kernel and temporal blocks k > 1 fall back to those) and
+ * cannot be batch members.  Takes effect from the next step.
  * FHP_EINVAL for other values. */
 #define FHP_RULES_FHP_I 1
 #define FHP_RULES_FHP_II 2
@@ -259,7 +260,7 @@ FHP_API int fhp_autotune(fhp_lattice* lattice, int32_t trial_steps, int32_t* out
  * fall back to 1 when a row does not fit a stage; automatic picks 1 for
  * lattices of fewer than 8 tiles, 4 (with exchanges every second step where
  * the strips allow it) for lattices of fewer than 2 tiles per SM whose strips
- * fit, 3 up to 24 tiles per SM and 2 above; FHP-III lattices always run 1.
+ * fit, 3 up to 24 tiles per SM and 2 above (FHP-III lattices: never 4).
  * Results are identical for every choice.  While the kernel is automatic and the temporal block 1, a
  * configuration recorded by fhp_autotune for the lattice's description takes
  * precedence. */
@@ -443,7 +444,11 @@ FHP_API int64_t fhp_batch_kernel_launches(const fhp_batch* batch);
  * 4096 x 4096 does not); larger lattices fail with FHP_EINVAL.
  * The first call on a device looks the array's device address up
  * (cudaGetSymbolAddress, with that device current); make that first call
- * before any stream capture.  Every call on a device shares the array and it
+ * before any stream capture.  The address is kept for the device's context
+ * and looked up again if that context was destroyed and made again
+ * (cudaDeviceReset).  Steps run on the direct step kernel, which has no
+ * device-side waits, so nothing can time out unseen in this asynchronous
+ * call.  Every call on a device shares the array and it
  * keeps the previous call's contents (the call rewrites all of it that it
  * reads, and clears the flag word); calls whose GPU work overlaps -- from
  * different streams or host threads -- race on it and must be serialised by

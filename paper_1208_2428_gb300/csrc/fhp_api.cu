@@ -127,26 +127,6 @@ Layout layout(int32_t W, int32_t H) {
     return L;
 }
 
-// Forcing thresholds: P = round-half-even(p * 2^32); S_0 = 2^32,
-// S_g = floor(S_{g-1} (2^32 - P) / 2^32); Q_g = 2^32 - S_g.
-fhp::ForcingTable forcing_table(double p) {
-    const unsigned long long one = 1ULL << 32;
-    unsigned long long P;
-    const double scaled = std::ldexp(p, 32);
-    if (!(scaled > 0.0)) P = 0;
-    else if (scaled >= std::ldexp(1.0, 32)) P = one;
-    else P = (unsigned long long)std::nearbyint(scaled);  // default mode: nearest, ties to even
-    fhp::ForcingTable ft;
-    unsigned long long S = one;
-    ft.p_plus_1 = P + 1;
-    ft.q[0] = 0;
-    for (int g = 1; g <= 32; ++g) {
-        S = (unsigned long long)(((unsigned __int128)S * (one - P)) >> 32);
-        ft.q[g] = one - S;
-    }
-    return ft;
-}
-
 // Makes the lattice's device current for the duration of a call.
 struct DeviceGuard {
     int prev = -1;
@@ -230,6 +210,31 @@ int read_solid_flag(fhp_lattice* h) {
 
 void fhp::set_thread_error(const char* message) { g_create_error = message; }
 
+fhp::ForcingTable fhp::forcing_table(double p) {
+    const unsigned long long one = 1ULL << 32;
+    unsigned long long P;
+    const double scaled = std::ldexp(p, 32);   // exact: a power-of-two scaling
+    if (!(scaled > 0.0)) {
+        P = 0;
+    } else if (scaled >= std::ldexp(1.0, 32)) {
+        P = one;
+    } else {
+        // scaled < 2^32: its integer part fits, and scaled - floor(scaled) is exact.
+        const unsigned long long ip = (unsigned long long)scaled;   // truncation = floor for scaled > 0
+        const double frac = scaled - (double)ip;
+        P = ip + ((frac > 0.5 || (frac == 0.5 && (ip & 1ull))) ? 1ull : 0ull);
+    }
+    fhp::ForcingTable ft;
+    unsigned long long S = one;
+    ft.p_plus_1 = P + 1;
+    ft.q[0] = 0;
+    for (int g = 1; g <= 32; ++g) {
+        S = (unsigned long long)(((unsigned __int128)S * (one - P)) >> 32);
+        ft.q[g] = one - S;
+    }
+    return ft;
+}
+
 extern "C" {
 
 size_t fhp_required_bytes(int32_t width, int32_t height) {
@@ -257,7 +262,7 @@ int fhp_create(fhp_lattice** out, const fhp_params* params) {
     h->g = fhp::make_geometry(W, H);
     h->seed = params->seed;
     h->p = params->forcing_p;
-    h->ft = forcing_table(h->p);
+    h->ft = fhp::forcing_table(h->p);
     h->force = h->ft.q[32] != 0;
     h->stream = (cudaStream_t)params->stream;
     const Layout L = layout(W, H);
@@ -533,7 +538,7 @@ int fhp_set_forcing(fhp_lattice* h, double p) {
     if (!h) return fail(nullptr, FHP_EINVAL, "lattice is NULL");
     if (!(p >= 0.0 && p <= 1.0)) return fail(h, FHP_EINVAL, "forcing probability %g outside [0, 1]", p);
     h->p = p;
-    h->ft = forcing_table(p);
+    h->ft = fhp::forcing_table(p);
     h->force = h->ft.q[32] != 0;
     return FHP_OK;
 }

@@ -9,7 +9,7 @@
 //
 // fhp_batch_kernel is the warp-specialised ring of the single-lattice path
 // (producer warp streaming row tiles into a 3-stage shared-memory ring with
-// cp.async.bulk, 7 consumer warps computing), except that every tile may
+// cp.async.bulk, 8 consumer warps computing), except that every tile may
 // belong to a different lattice: the producer copies that lattice's
 // descriptor (geometry, buffers, generator key, step, forcing table) into a
 // per-stage header in shared memory, and the consumers run the same per-quad
@@ -35,11 +35,11 @@
 namespace fhp {
 namespace {
 
-constexpr int kBConsumerWarps = 7;   // 2 CTAs x 8 warps per SM: up to 128 registers, no spills
+constexpr int kBConsumerWarps = 8;
 constexpr int kBThreads = (kBConsumerWarps + 1) * 32;       // + producer warp
 constexpr int kBRunThreads = (kBConsumerWarps + 2) * 32;    // + producer and publisher warps
 constexpr int kBStages = 3;
-constexpr int kBStageBudget = 28 * 1024;
+constexpr int kBStageBudget = 32 * 1024;
 
 // Device descriptor of one member lattice.
 struct BatchLattice {
@@ -461,24 +461,6 @@ size_t member_bytes(const fhp::Geometry& g) {
     return 15 * fhp::round256(g.plane_words * sizeof(uint32_t)) + 256;
 }
 
-fhp::ForcingTable forcing_thresholds(double p) {
-    const unsigned long long one = 1ULL << 32;
-    unsigned long long P;
-    const double scaled = std::ldexp(p, 32);
-    if (!(scaled > 0.0)) P = 0;
-    else if (scaled >= std::ldexp(1.0, 32)) P = one;
-    else P = (unsigned long long)std::nearbyint(scaled);
-    fhp::ForcingTable ft;
-    unsigned long long S = one;
-    ft.p_plus_1 = P + 1;
-    ft.q[0] = 0;
-    for (int g = 1; g <= 32; ++g) {
-        S = (unsigned long long)(((unsigned __int128)S * (one - P)) >> 32);
-        ft.q[g] = one - S;
-    }
-    return ft;
-}
-
 struct DeviceGuard {
     int prev = -1;
     explicit DeviceGuard(int dev) {
@@ -589,10 +571,8 @@ int ensure_tables(fhp_batch* b, size_t lats, size_t tiles) {
     return FHP_OK;
 }
 
-// Rows per tile: about one quad per consumer thread (224 per tile), and the
-// tile's 8 planes within one stage.  Seven consumer warps (two CTAs of eight
-// warps per SM) leave room for 112 registers without spills; eight measured
-// 5 % slower on the 512-lattice ensemble (96 registers with spills).
+// Rows per tile: about one quad per consumer thread (256 per tile), and the
+// tile's 8 planes within one stage.
 int rows_per_tile(const fhp::Geometry& g) {
     const long long row_bytes = 8LL * g.Pq * 4;
     int R = (fhp::kBConsumerWarps * 32 + g.nq - 1) / g.nq;
@@ -692,7 +672,7 @@ int fhp_batch_add(fhp_batch* b, int32_t width, int32_t height, uint64_t seed, do
     m.g = g;
     m.seed = seed;
     m.p = forcing_p;
-    m.ft = forcing_thresholds(forcing_p);
+    m.ft = fhp::forcing_table(forcing_p);
     m.bytes = member_bytes(g);
     m.off = b->arena.allocate(m.bytes);
     if (m.off == SIZE_MAX) return bfail(b, FHP_ENOMEM, "batch arena full: a %d x %d lattice needs %zu bytes", width, height, m.bytes);
@@ -1221,8 +1201,10 @@ int fhp_batch_step(fhp_batch* b, int64_t n) {
         }
     }
     while (left > 0) {
-        // Calls are split into chunks of at most 2^24 steps (the multi-step
-        // kernel's counters hold 8 per tile and step).
+        // Calls are split into chunks of at most 2^24 steps: the multi-step
+        // kernel's counters grow by kBConsumerWarps per tile and step.
+        static_assert((unsigned long long)fhp::kBConsumerWarps << 24 <= 0xFFFFFFFFull,
+                      "tile counters of a 2^24-step chunk must fit in 32 bits");
         const int chunk = (int)std::min<int64_t>(left, (int64_t)1 << 24);
         int kind = b->step_kernel;
         if (kind == FHP_BATCH_KERNEL_AUTO) {

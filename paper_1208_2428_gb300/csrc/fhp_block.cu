@@ -228,7 +228,7 @@ cudaError_t launch_block_variant(const StepArgs& a, const BlockArgs& b, cudaStre
 
 bool block_supported(const Geometry& g, int k) {
     return (k == 2 || k == 4 || k == 8) && g.Wq % 4 == 0 && g.nq >= 4 && g.H >= 2 * k + 2 && 2 * k < kRin &&
-           g.rules != 3;   // FHP-III: direct kernel only
+           g.rules != 3;   // FHP-III: not in the blocked kernel
 }
 
 cudaError_t launch_block(const Geometry& g, const uint32_t* src, uint32_t* dst, const uint32_t* solid,

@@ -34,8 +34,14 @@ struct Geometry {
     int Pq = 0;         // row pitch in words (multiple of 4)
     size_t plane_words = 0;  // H * Pq
     int row_base = 0;   // lattice row of array row 0 (a strip of a larger lattice; even)
-    int rules = 2;      // collision rule set: 2 = FHP-II, 1 = FHP-I, 3 = FHP-III (direct kernel only)
+    int rules = 2;      // collision rule set: 2 = FHP-II, 1 = FHP-I, 3 = FHP-III (direct and ring kernels)
 };
+
+// Forcing thresholds of probability p (host): P = round-half-even(p * 2^32),
+// computed from the integer and fraction parts of the exact double p * 2^32
+// (independent of the floating-point rounding mode); S_0 = 2^32,
+// S_g = floor(S_{g-1} (2^32 - P) / 2^32), Q_g = 2^32 - S_g (exact integers).
+ForcingTable forcing_table(double p);
 
 // Mask that enables the rest-particle rules of the bit-sliced scattering.
 inline uint32_t rest_rules_mask(const Geometry& g) { return g.rules == 1 ? 0u : 0xFFFFFFFFu; }

@@ -203,7 +203,7 @@ __device__ void issue_tile(const StepArgs& a, const TileArgs& ta, const uint32_t
     }
 }
 
-template <bool SOLID, bool FORCE, bool RAGGED>
+template <bool SOLID, bool FORCE, bool RAGGED, bool SAT = false>
 __device__ __forceinline__ void quad_from_stage(const StepArgs& a, const StepVar& v, const TileArgs& ta,
                                                 const uint32_t* stage, int r, int y, int q) {
     const int Pq = a.Pq, R = ta.R;
@@ -237,10 +237,11 @@ __device__ __forceinline__ void quad_from_stage(const StepArgs& a, const StepVar
         n3 = i3;
         n1 = i1;
     }
-    finish_quad<SOLID, FORCE, RAGGED>(a, v, q, y, m, n0, n1, n2, n3, n4, n5, i6, sd, true);
+    finish_quad<SOLID, FORCE, RAGGED, SAT>(a, v, q, y, m, n0, n1, n2, n3, n4, n5, i6, sd, true);
 }
 
-template <bool SOLID, bool FORCE, bool RAGGED>
+// SAT selects the FHP-III rule set (collision-saturated scattering).
+template <bool SOLID, bool FORCE, bool RAGGED, bool SAT = false>
 __device__ __forceinline__ void compute_tile(const StepArgs& a, const StepVar& v, const TileArgs& ta, int tile,
                                              const uint32_t* stage, int tid, int nthreads) {
     const int y0 = tile * ta.R;
@@ -256,7 +257,7 @@ __device__ __forceinline__ void compute_tile(const StepArgs& a, const StepVar& v
         const int k = (int)(((unsigned long long)j * ta.nq_magic) >> 32);  // j / nq
         const int q = (int)j - k * a.nq;
         const int r = 2 * k + h;
-        quad_from_stage<SOLID, FORCE, RAGGED>(a, v, ta, stage, r, y0 + r, q);
+        quad_from_stage<SOLID, FORCE, RAGGED, SAT>(a, v, ta, stage, r, y0 + r, q);
     }
 }
 

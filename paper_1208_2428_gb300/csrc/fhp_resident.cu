@@ -218,7 +218,7 @@ size_t resident_halo_words(const Geometry& g, int gh) {
 }
 
 bool resident_supported(const Geometry& g, bool has_solid, size_t staging_bytes, int gh) {
-    if ((gh != 1 && gh != 2) || g.rules == 3) return false;   // FHP-III: direct kernel only
+    if ((gh != 1 && gh != 2) || g.rules == 3) return false;   // FHP-III: not in the resident kernels
     const int grid = resident_grid(g);
     if (grid <= 0) return false;
     if (gh > 1 && g.H / grid < 2 * gh) return false;   // every strip holds its 2 gh edge rows

@@ -30,19 +30,55 @@ static __device__ __align__(256) unsigned char g_static_scratch[kScratchBytes];
 
 std::mutex g_mutex;
 void* g_scratch_addr[kMaxDevices] = {};
+unsigned long long g_scratch_ctx[kMaxDevices] = {};   // context the address belongs to
 
 size_t round256(size_t v) { return (v + 255) / 256 * 256; }
 
-// Device address of the scratch array on the current device.  The first call
-// on a device looks it up (cudaGetSymbolAddress, with that device current);
-// later calls reuse it.
+// Identity of the calling thread's current CUDA context (0 if none or if the
+// driver cannot say), from the driver's cuCtxGetCurrent and cuCtxGetId looked
+// up through the runtime (no link against the driver library).
+typedef int (*CtxGetCurrentFn)(void**);
+typedef int (*CtxGetIdFn)(void*, unsigned long long*);
+
+unsigned long long current_context_id() {
+    static std::once_flag once;
+    static CtxGetCurrentFn get_current = nullptr;
+    static CtxGetIdFn get_id = nullptr;
+    std::call_once(once, [] {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = (CtxGetCurrentFn)f;
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = (CtxGetIdFn)f;
+        cudaGetLastError();
+    });
+    void* ctx = nullptr;
+    unsigned long long id = 0;
+    if (!get_current || !get_id || get_current(&ctx) != 0 || !ctx || get_id(ctx, &id) != 0) return 0;
+    return id;
+}
+
+// Device address of the scratch array on the current device.  Set-up, once
+// per device (with that device current): cudaGetSymbolAddress, which needs no
+// allocation, its result checked and kept.  A later call reuses it while the
+// device's context is the same one; after the context was destroyed and made
+// again (cudaDeviceReset) the module may sit elsewhere, so the address is
+// looked up again.  If the context's identity cannot be read, every call
+// looks the address up.
 cudaError_t scratch_address(int device, void** out) {
     std::lock_guard<std::mutex> lock(g_mutex);
-    if (!g_scratch_addr[device]) {
+    const unsigned long long ctx = current_context_id();
+    if (!g_scratch_addr[device] || ctx == 0 || ctx != g_scratch_ctx[device]) {
         void* p = nullptr;
         const cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
         if (e != cudaSuccess) return e;
         g_scratch_addr[device] = p;
+        // The look-up initialises the context if it did not exist yet.
+        g_scratch_ctx[device] = ctx ? ctx : current_context_id();
     }
     *out = g_scratch_addr[device];
     return cudaSuccess;
@@ -51,25 +87,6 @@ cudaError_t scratch_address(int device, void** out) {
 int fail(int code, const char* msg) {
     fhp::set_thread_error(msg);  // reported by fhp_last_error(NULL)
     return code;
-}
-
-// Forcing thresholds Q_g of the geometric-skipping sampler (see fhp_api.cu).
-fhp::ForcingTable thresholds(double p) {
-    const unsigned long long one = 1ULL << 32;
-    unsigned long long P;
-    const double scaled = std::ldexp(p, 32);
-    if (!(scaled > 0.0)) P = 0;
-    else if (scaled >= std::ldexp(1.0, 32)) P = one;
-    else P = (unsigned long long)std::nearbyint(scaled);
-    fhp::ForcingTable ft;
-    unsigned long long S = one;
-    ft.p_plus_1 = P + 1;
-    ft.q[0] = 0;
-    for (int g = 1; g <= 32; ++g) {
-        S = (unsigned long long)(((unsigned __int128)S * (one - P)) >> 32);
-        ft.q[g] = one - S;
-    }
-    return ft;
 }
 
 }  // namespace
@@ -110,14 +127,17 @@ extern "C" FHP_API int fhp_run_static(const uint8_t* device_bytes_in, uint8_t* d
     // only the flag word has to start at zero.
     e = cudaMemsetAsync(flag, 0, sizeof(unsigned int), s);
     if (e == cudaSuccess) e = fhp::launch_pack(g, device_bytes_in, buf[0], solid, flag, s);
-    const fhp::ForcingTable ft = thresholds(forcing_p);
+    const fhp::ForcingTable ft = fhp::forcing_table(forcing_p);
     const bool force = ft.q[32] != 0;
     const fhp::Key2 key{(uint32_t)seed, (uint32_t)(seed >> 32)};
     int cur = 0;
     for (int64_t i = 0; i < n && e == cudaSuccess; ++i) {
         // The solid plane is always read (it is all zero when there are no
-        // obstacles), so no host read-back of the solid flag is needed.
-        e = fhp::launch_step(g, buf[cur], buf[cur ^ 1], solid, true, force, ft, key, (uint64_t)(t0 + i), s);
+        // obstacles), so no host read-back of the solid flag is needed.  The
+        // direct kernel is used because it has no device-side waits: the
+        // call is asynchronous and could not report a wait that gave up.
+        e = fhp::launch_step(g, buf[cur], buf[cur ^ 1], solid, true, force, ft, key, (uint64_t)(t0 + i), s,
+                             nullptr, fhp::kStepDirect);
         cur ^= 1;
     }
     if (e == cudaSuccess) e = fhp::launch_unpack(g, buf[cur], solid, device_bytes_out, s);

@@ -48,8 +48,10 @@ constexpr int kBarrierBytes = 128;      // mbarriers at the front of shared memo
 // the copies' bytes) release a stage to the consumer warps, and "empty"
 // barriers (one arrival per consumer warp) hand it back.  No block-wide
 // barrier is taken after set-up, and every wait is bounded.
-template <bool SOLID, bool FORCE, bool RAGGED>
-__global__ void __launch_bounds__(kTmaThreads, 2) fhp_step_tma_kernel(const StepArgs a, const TileArgs ta) {
+// SAT: the FHP-III rule set; its larger scattering network gets one CTA per
+// SM and the registers of two.
+template <bool SOLID, bool FORCE, bool RAGGED, bool SAT>
+__global__ void __launch_bounds__(kTmaThreads, SAT ? 1 : 2) fhp_step_tma_kernel(const StepArgs a, const TileArgs ta) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw);
     uint64_t* empty = full + kStages;
@@ -98,8 +100,8 @@ __global__ void __launch_bounds__(kTmaThreads, 2) fhp_step_tma_kernel(const Step
             if (lane == 0 && a.err) atomicOr(a.err, 1u);
             return;
         }
-        compute_tile<SOLID, FORCE, RAGGED>(a, v, ta, tile_of(i), stage_of(i), (int)threadIdx.x,
-                                           kConsumerWarps * 32);
+        compute_tile<SOLID, FORCE, RAGGED, SAT>(a, v, ta, tile_of(i), stage_of(i), (int)threadIdx.x,
+                                                kConsumerWarps * 32);
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[s]);
     }
@@ -127,9 +129,9 @@ struct RunArgs {
     unsigned long long t0;
 };
 
-template <bool SOLID, bool FORCE, bool RAGGED>
-__global__ void __launch_bounds__(kRunThreads, 2) fhp_run_kernel(const StepArgs a, const TileArgs ta,
-                                                                 const RunArgs ra) {
+template <bool SOLID, bool FORCE, bool RAGGED, bool SAT>
+__global__ void __launch_bounds__(kRunThreads, SAT ? 1 : 2) fhp_run_kernel(const StepArgs a, const TileArgs ta,
+                                                                           const RunArgs ra) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw);
     uint64_t* empty = full + kStages;  // all consumer warps finished the stage's tile
@@ -245,8 +247,8 @@ __global__ void __launch_bounds__(kRunThreads, 2) fhp_run_kernel(const StepArgs 
                 if (lane == 0 && a.err) atomicOr(a.err, 1u);
                 return;
             }
-            compute_tile<SOLID, FORCE, RAGGED>(a, v, ta, tile, stages + (size_t)st * stage_words,
-                                               (int)threadIdx.x, kConsumerWarps * 32);
+            compute_tile<SOLID, FORCE, RAGGED, SAT>(a, v, ta, tile, stages + (size_t)st * stage_words,
+                                                    (int)threadIdx.x, kConsumerWarps * 32);
             __syncwarp();
             if (lane == 0) {
                 mbar_arrive(&empty[st]);                        // the stage may be refilled
@@ -362,8 +364,8 @@ __device__ __forceinline__ void direct_quad(const StepArgs& a, const Lane& L) {
     finish_quad<SOLID, FORCE, RAGGED, SAT>(a, v, L.q, y, m, n0, n1, n2, n3, n4, n5, i6, sd, L.active);
 }
 
-// SAT: the FHP-III rule set (the only kernel that carries it; its larger
-// scattering network gets twice the registers).
+// SAT: the FHP-III rule set (its larger scattering network gets twice the
+// registers).
 template <bool SOLID, bool FORCE, bool RAGGED, bool SAT>
 __global__ void __launch_bounds__(kBlock, SAT ? 2 : 4) fhp_step_direct_kernel(const StepArgs a) {
     const Lane L = map_lane(a);
@@ -389,22 +391,22 @@ __global__ void philox_kernel(const uint32_t* __restrict__ ctr, const uint32_t* 
 // ---------------------------------------------------------------------------
 struct DeviceInfo {
     int sms = 0;
-    int tma_blocks_per_sm[8] = {};  // per kernel variant (solid, force, ragged)
-    bool configured[8] = {};
-    int run_blocks_per_sm[8] = {};
-    bool run_configured[8] = {};
+    int tma_blocks_per_sm[16] = {};  // per kernel variant (sat, solid, force, ragged)
+    bool configured[16] = {};
+    int run_blocks_per_sm[16] = {};
+    bool run_configured[16] = {};
 };
 std::mutex g_dev_mutex;
 DeviceInfo g_dev[64];
 
-template <bool SOLID, bool FORCE, bool RAGGED>
+template <bool SOLID, bool FORCE, bool RAGGED, bool SAT>
 cudaError_t launch_tma_variant(const StepArgs& a, const TileArgs& ta, size_t smem, cudaStream_t s) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
-    const int variant = (SOLID ? 4 : 0) | (FORCE ? 2 : 0) | (RAGGED ? 1 : 0);
-    auto kernel = fhp_step_tma_kernel<SOLID, FORCE, RAGGED>;
+    const int variant = (SAT ? 8 : 0) | (SOLID ? 4 : 0) | (FORCE ? 2 : 0) | (RAGGED ? 1 : 0);
+    auto kernel = fhp_step_tma_kernel<SOLID, FORCE, RAGGED, SAT>;
     int blocks_per_sm, sms;
     {
         std::lock_guard<std::mutex> lock(g_dev_mutex);
@@ -431,15 +433,15 @@ cudaError_t launch_tma_variant(const StepArgs& a, const TileArgs& ta, size_t sme
     return cudaGetLastError();
 }
 
-template <bool SOLID, bool FORCE, bool RAGGED>
+template <bool SOLID, bool FORCE, bool RAGGED, bool SAT>
 cudaError_t launch_run_variant(const StepArgs& a, const TileArgs& ta, const RunArgs& ra, size_t smem,
                                cudaStream_t s) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
-    const int variant = (SOLID ? 4 : 0) | (FORCE ? 2 : 0) | (RAGGED ? 1 : 0);
-    auto kernel = fhp_run_kernel<SOLID, FORCE, RAGGED>;
+    const int variant = (SAT ? 8 : 0) | (SOLID ? 4 : 0) | (FORCE ? 2 : 0) | (RAGGED ? 1 : 0);
+    auto kernel = fhp_run_kernel<SOLID, FORCE, RAGGED, SAT>;
     int blocks_per_sm, sms;
     {
         std::lock_guard<std::mutex> lock(g_dev_mutex);
@@ -475,15 +477,21 @@ cudaError_t launch_run_variant(const StepArgs& a, const TileArgs& ta, const RunA
 
 template <bool SOLID, bool FORCE>
 cudaError_t launch_run(const StepArgs& a, const TileArgs& ta, const RunArgs& ra, size_t smem, bool ragged,
-                       cudaStream_t s) {
-    return ragged ? launch_run_variant<SOLID, FORCE, true>(a, ta, ra, smem, s)
-                  : launch_run_variant<SOLID, FORCE, false>(a, ta, ra, smem, s);
+                       bool sat, cudaStream_t s) {
+    if (sat)
+        return ragged ? launch_run_variant<SOLID, FORCE, true, true>(a, ta, ra, smem, s)
+                      : launch_run_variant<SOLID, FORCE, false, true>(a, ta, ra, smem, s);
+    return ragged ? launch_run_variant<SOLID, FORCE, true, false>(a, ta, ra, smem, s)
+                  : launch_run_variant<SOLID, FORCE, false, false>(a, ta, ra, smem, s);
 }
 
 template <bool SOLID, bool FORCE>
-cudaError_t launch_tma(const StepArgs& a, const TileArgs& ta, size_t smem, bool ragged, cudaStream_t s) {
-    return ragged ? launch_tma_variant<SOLID, FORCE, true>(a, ta, smem, s)
-                  : launch_tma_variant<SOLID, FORCE, false>(a, ta, smem, s);
+cudaError_t launch_tma(const StepArgs& a, const TileArgs& ta, size_t smem, bool ragged, bool sat, cudaStream_t s) {
+    if (sat)
+        return ragged ? launch_tma_variant<SOLID, FORCE, true, true>(a, ta, smem, s)
+                      : launch_tma_variant<SOLID, FORCE, false, true>(a, ta, smem, s);
+    return ragged ? launch_tma_variant<SOLID, FORCE, true, false>(a, ta, smem, s)
+                  : launch_tma_variant<SOLID, FORCE, false, false>(a, ta, smem, s);
 }
 
 template <bool SOLID, bool FORCE>
@@ -532,7 +540,7 @@ Geometry make_geometry(int W, int H) {
 
 int resolved_step_kernel(const Geometry& g, bool has_solid, int requested) {
     const int R = tile_rows(g, has_solid);
-    if (R == 0 || requested == kStepDirect || g.rules == 3) return kStepDirect;   // FHP-III: direct kernel only
+    if (R == 0 || requested == kStepDirect) return kStepDirect;
     if (requested == kStepRing || requested == kStepRun) return requested;
     int dev = 0, sms = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return kStepDirect;
@@ -594,11 +602,12 @@ cudaError_t launch_run(const Geometry& g, uint32_t* buf0, uint32_t* buf1, const 
     if (e != cudaSuccess) return e;
     const size_t smem = kBarrierBytes + (size_t)kStages * (has_solid ? 8 : 7) * R * g.Pq * 4;
     const bool ragged = (g.Wq % 4) != 0;
+    const bool sat = g.rules == 3;
     if (has_solid)
-        return force ? launch_run<true, true>(a, ta, ra, smem, ragged, stream)
-                     : launch_run<true, false>(a, ta, ra, smem, ragged, stream);
-    return force ? launch_run<false, true>(a, ta, ra, smem, ragged, stream)
-                 : launch_run<false, false>(a, ta, ra, smem, ragged, stream);
+        return force ? launch_run<true, true>(a, ta, ra, smem, ragged, sat, stream)
+                     : launch_run<true, false>(a, ta, ra, smem, ragged, sat, stream);
+    return force ? launch_run<false, true>(a, ta, ra, smem, ragged, sat, stream)
+                 : launch_run<false, false>(a, ta, ra, smem, ragged, sat, stream);
 }
 
 cudaError_t launch_step(const Geometry& g, const uint32_t* src, uint32_t* dst,
@@ -630,11 +639,12 @@ cudaError_t launch_step(const Geometry& g, const uint32_t* src, uint32_t* dst,
         ta.nq_magic = ((1ull << 32) + g.nq - 1) / g.nq;
         a.rows_per_warp = a.groups_per_parity = a.warps_per_row = 1;
         const size_t smem = kBarrierBytes + (size_t)kStages * (has_solid ? 8 : 7) * R * g.Pq * 4;
+        const bool sat = g.rules == 3;
         if (has_solid)
-            return force ? launch_tma<true, true>(a, ta, smem, ragged, stream)
-                         : launch_tma<true, false>(a, ta, smem, ragged, stream);
-        return force ? launch_tma<false, true>(a, ta, smem, ragged, stream)
-                     : launch_tma<false, false>(a, ta, smem, ragged, stream);
+            return force ? launch_tma<true, true>(a, ta, smem, ragged, sat, stream)
+                         : launch_tma<true, false>(a, ta, smem, ragged, sat, stream);
+        return force ? launch_tma<false, true>(a, ta, smem, ragged, sat, stream)
+                     : launch_tma<false, false>(a, ta, smem, ragged, sat, stream);
     }
     long long warps;
     if (g.nq >= 32) {

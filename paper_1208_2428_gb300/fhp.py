@@ -286,7 +286,7 @@ class Lattice:
     # -- collision rules -------------------------------------------------------------
     def set_rules(self, rules: int):
         """2: FHP-II (default); 1: FHP-I (no rest-particle collisions); 3: FHP-III
-        (collision-saturated; steps with the direct kernel only)."""
+        (collision-saturated; steps with the direct and ring kernels)."""
         self._check(self._lib.fhp_set_rules(self._h, int(rules)))
 
     @property

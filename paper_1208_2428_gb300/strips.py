@@ -111,16 +111,18 @@ class LocalExchange:
 
 
 class DistExchange:
-    """One strip per rank of a torch.distributed process group (gloo for
-    host tensors, NCCL for device tensors).  With a single rank the strip
-    exchanges with itself (periodic wrap)."""
+    """One strip per rank of a torch.distributed process group.  NCCL moves
+    device tensors directly; on a gloo group the rows of device strips are
+    staged through host memory (``via_host``, the default for gloo).  With a
+    single rank the strip exchanges with itself (periodic wrap)."""
 
-    def __init__(self, group=None):
+    def __init__(self, group=None, via_host=None):
         import torch.distributed as dist
         self.dist = dist
         self.group = group
         self.rank = dist.get_rank(group)
         self.size = dist.get_world_size(group)
+        self.via_host = (dist.get_backend(group) == "gloo") if via_host is None else bool(via_host)
 
     def exchange(self, plan: StripPlan, strips: list):
         if len(strips) != 1 or plan.parts != self.size:
@@ -132,8 +134,15 @@ class DistExchange:
             s.set_rows(plan.ghost_above_rows(r)[0], down)
             s.set_rows(plan.ghost_below_rows(r)[0], up)
             return
-        from_above = s.empty_rows(plan.halo)
-        from_below = s.empty_rows(plan.halo)
+        import torch
+        device = down.device if (self.via_host and down.is_cuda) else None
+        if device is not None:
+            # The rows were gathered on the strip's stream: wait, then stage
+            # them in host memory for the host-memory backend.
+            torch.cuda.synchronize(device)
+            down, up = down.cpu(), up.cpu()
+        from_above = torch.empty_like(down)
+        from_below = torch.empty_like(down)
         below, above = plan.below(r), plan.above(r)
         ops = [dist.P2POp(dist.isend, down, below, self.group), dist.P2POp(dist.isend, up, above, self.group),
                dist.P2POp(dist.irecv, from_above, above, self.group),
@@ -146,6 +155,9 @@ class DistExchange:
                    dist.P2POp(dist.irecv, from_below, below, self.group, tag=2)]
         for req in dist.batch_isend_irecv(ops):
             req.wait()
+        if device is not None:
+            from_above, from_below = from_above.to(device), from_below.to(device)
+            torch.cuda.synchronize(device)
         s.set_rows(plan.ghost_above_rows(r)[0], from_above)
         s.set_rows(plan.ghost_below_rows(r)[0], from_below)
 

@@ -2,10 +2,12 @@
 
 It serves callers that cannot allocate device memory (plugins whose host
 application owns all GPU memory, services with a fixed memory cap, loops that
-must not allocate).  Its output must equal what the ordinary lattice calls
-(fhp_create, fhp_set_state, fhp_set_time, fhp_step, fhp_get_state) give --
-bit-exact, the tolerance of every lattice-state test here -- on consecutive
-calls that reuse the same static scratch array.  This file is collected last
+must not allocate).  Its output must equal the CPU oracle's run and what the ordinary lattice
+calls (fhp_create, fhp_set_state, fhp_set_time, fhp_step, fhp_get_state) give
+-- bit-exact, the tolerance of every lattice-state test here -- on
+consecutive calls that reuse the same static scratch array: with and without
+obstacles, in place (input and output the same buffer) and at the largest
+size the header documents.  This file is collected last
 so that a run that stops at the first failure has run every other test.
 """
 import ctypes
@@ -34,11 +36,11 @@ def lib():
     return lib
 
 
-def run_static(lib, s0, seed, t0, n, p):
+def run_static(lib, s0, seed, t0, n, p, in_place=False):
     import torch
     H, W = s0.shape
     din = torch.from_numpy(s0).cuda()
-    dout = torch.full_like(din, 0x5A)
+    dout = din if in_place else torch.full_like(din, 0x5A)
     stream = torch.cuda.current_stream()
     rc = lib.fhp_run_static(ctypes.c_void_p(din.data_ptr()), ctypes.c_void_p(dout.data_ptr()), W, H,
                             seed, t0, n, p, ctypes.c_void_p(stream.cuda_stream))
@@ -57,20 +59,36 @@ def run_lattice(s0, seed, t0, n, p):
         return lat.get_state()
 
 
-def test_run_static_matches_lattice_calls(lib):
+def run_oracle(s0, seed, t0, n, p):
+    import oracle
+    return oracle.run(s0, seed, t0, n, p)[0]
+
+
+def test_run_static_matches_lattice_calls_and_oracle(lib):
     W1, H1 = 4160, 64
     a = workloads.bernoulli_lattice(W1, H1, 0.3, 31, workloads.cylinder_mask(W1, H1))
     rng = np.random.Generator(np.random.PCG64(32))
     W2, H2 = 224, 30
     b = workloads.bernoulli_lattice(W2, H2, 0.4, 33, workloads.random_points(W2, H2, 0.05, rng))
-    calls = [(a, 0xABCDEF0123, 7, 21, 0.02), (b, 99, 0, 13, 0.0), (a, 0xABCDEF0123, 7, 21, 0.02)]
+    W3, H3 = 640, 48
+    c = workloads.bernoulli_lattice(W3, H3, 0.25, 34)     # no obstacles: the solid plane is all zero
+    calls = [(a, 0xABCDEF0123, 7, 21, 0.02, False), (b, 99, 0, 13, 0.0, False), (c, 5, 3, 17, 0.01, False),
+             (b, 99, 0, 13, 0.0, True), (a, 0xABCDEF0123, 7, 21, 0.02, False)]
     outs = []
-    for s0, seed, t0, n, p in calls:   # consecutive calls share the static scratch array
-        got = run_static(lib, s0, seed, t0, n, p)
-        want = run_lattice(s0, seed, t0, n, p)
-        assert np.array_equal(got, want)
+    for s0, seed, t0, n, p, in_place in calls:   # consecutive calls share the static scratch array
+        got = run_static(lib, s0, seed, t0, n, p, in_place=in_place)
+        assert np.array_equal(got, run_oracle(s0, seed, t0, n, p))
+        assert np.array_equal(got, run_lattice(s0, seed, t0, n, p))
         outs.append(got)
-    assert np.array_equal(outs[0], outs[2])
+    assert np.array_equal(outs[0], outs[4])
+    assert np.array_equal(outs[1], outs[3])     # in place == separate buffers
+
+
+def test_run_static_largest_documented_lattice(lib):
+    W, H = 4096, 2048                            # the size limit stated in the header
+    s0 = workloads.bernoulli_lattice(W, H, 0.2, 35, workloads.channel_walls(W, H))
+    got = run_static(lib, s0, 41, 0, 2, 1e-3)
+    assert np.array_equal(got, run_oracle(s0, 41, 0, 2, 1e-3))
 
 
 def test_run_static_rejects_oversized_lattice(lib):
