@@ -152,17 +152,23 @@ FHP_API int fhp_set_time(fhp_lattice* lattice, int64_t t);
 /* Change the forcing probability (in [0, 1]) for subsequent steps. */
 FHP_API int fhp_set_forcing(fhp_lattice* lattice, double p);
 
-/* Number of steps fused into one kernel pass (temporal blocking): 1, 2, 4
- * or 8.  With k > 1, fhp_step runs passes that stage a tile of the lattice
- * plus a halo of k rows and k words (forcing couples the 32 nodes of a word)
- * in shared memory and apply k steps there before writing the tile back, so
- * HBM is read and written once per k steps; leftover steps (n mod k) and
- * lattices the blocked kernel does not support (W not a multiple of 128,
- * fewer than 512 nodes per row, H < 2k + 2, or the FHP-III rule set) use the
- * single-step kernels.  With step kernel 4 (resident) the value is instead
- * the number of steps between exchanges of strip rows: 2 selects the
- * two-ghost-row variant where every strip holds at least 4 rows, other values
- * the one-row exchange.  Results are identical for every value.  Default 1. */
+/* Number of steps fused into one kernel pass (temporal blocking): 1, 2, 3,
+ * 4 or 8.  With k > 1, fhp_step runs passes that read the state from HBM
+ * once, apply k steps on chip and write the result once.  Two kernels do it:
+ *  - row wavefronts (k = 2, 3, 4) where a full row of every intermediate time
+ *    level fits shared memory (FHP-I/II lattices up to about 16,384 nodes per
+ *    row for k = 2 and 3, about 8,192 for k = 4): each CTA streams a band of
+ *    whole rows through per-level row rings, recomputing only the k - 1 rows
+ *    of each intermediate level beyond each band edge;
+ *  - 2-D tiles (k = 2, 4, 8) elsewhere: a tile plus a halo of k rows and k
+ *    words (forcing couples the 32 nodes of a word) is staged in shared
+ *    memory (W a multiple of 128, at least 512 nodes per row, H >= 2k + 2).
+ * Leftover steps (n mod k) and lattices neither kernel supports (and FHP-III
+ * lattices) use the single-step kernels.  With step kernel 4 (resident) the
+ * value is instead the number of steps between exchanges of strip rows: 2
+ * selects the two-ghost-row variant where every strip holds at least 4 rows,
+ * other values the one-row exchange.  Results are identical for every value.
+ * Default 1. */
 FHP_API int fhp_set_temporal_block(fhp_lattice* lattice, int32_t k);
 
 /* Obstacles generated on the device from simple shapes (the walls and
@@ -231,10 +237,20 @@ FHP_API int fhp_set_rows_device(fhp_lattice* lattice, int32_t y0, int32_t n, con
  * -1 for a NULL lattice. */
 FHP_API int fhp_get_temporal_block(const fhp_lattice* lattice);
 
+/* Kernel of the temporally blocked passes: 0 = automatic (row wavefronts
+ * where they support the lattice, else 2-D tiles; default), 1 = row
+ * wavefronts, 2 = 2-D tiles; a kernel that does not support the lattice or k
+ * falls back to the other one.  Results are identical for every choice.
+ * FHP_EINVAL for other values.  fhp_get_temporal_block_kernel returns the
+ * kernel fhp_step will use for the current settings: 1 or 2, 0 when no
+ * blocked pass runs (k = 1, or the resident kernel), -1 for NULL. */
+FHP_API int fhp_set_temporal_block_kernel(fhp_lattice* lattice, int32_t kind);
+FHP_API int fhp_get_temporal_block_kernel(const fhp_lattice* lattice);
+
 /* Autotuner.  Times every step configuration that applies to this lattice --
  * direct, ring, multi-step and resident kernels (the resident one with
  * exchanges every step and every second step), and temporal blocks
- * k = 2, 4, 8 --
+ * k = 2, 3, 4, 8 --
  * over trial_steps steps each (a multiple of 8 in [8, 4096]; each candidate
  * runs once untimed, then timed with CUDA events on the lattice's stream) and
  * records the fastest for this device, lattice shape, rule set, and whether

@@ -38,6 +38,7 @@ struct fhp_lattice {
     int64_t t = 0;
     bool has_solid = false;
     int k_block = 1;
+    int block_kernel = 0;          // temporal-block kernel: 0 automatic, 1 row wavefronts, 2 tiles
     int step_kernel = fhp::kStepAuto;
     int64_t launches = 0;
     std::string err;
@@ -61,6 +62,7 @@ struct TuneKey {
 struct TuneChoice {
     int kernel;   // fhp::StepKernel other than kStepAuto
     int k;        // temporal block
+    int bk;       // temporal-block kernel (0 automatic, 1 row wavefronts, 2 tiles)
 };
 std::mutex g_tune_mutex;
 std::vector<std::pair<TuneKey, TuneChoice>> g_tuned;
@@ -146,14 +148,16 @@ struct DeviceGuard {
 // holds whose multi-step ring would give fewer than two tiles per SM
 // (launch-bound sizes, where it measured fastest: 1163 vs 957 GSUPS on
 // 4096 x 1024, 1979 vs 1573 on 4096 x 2048).
-void effective_settings(const fhp_lattice* h, int* kernel, int* k_block) {
+void effective_settings(const fhp_lattice* h, int* kernel, int* k_block, int* bk = nullptr) {
     *kernel = h->step_kernel;
     *k_block = h->k_block;
+    if (bk) *bk = h->block_kernel;
     if (h->step_kernel != fhp::kStepAuto || h->k_block != 1) return;
     TuneChoice c;
     if (tuned_choice(TuneKey{h->device, h->g.W, h->g.H, h->has_solid, h->force, h->g.rules}, &c)) {
         *kernel = c.kernel;
         *k_block = c.k;
+        if (bk) *bk = c.bk;
         return;
     }
     const int resolved = fhp::resolved_step_kernel(h->g, h->has_solid, fhp::kStepAuto);
@@ -173,6 +177,16 @@ int resident_interval(const fhp_lattice* h, int kernel, int k_block) {
     if (kernel != fhp::kStepResident) return 0;
     if (k_block == 2 && fhp::resident_supported(h->g, h->has_solid, h->staging_bytes, 2)) return 2;
     return fhp::resident_supported(h->g, h->has_solid, h->staging_bytes, 1) ? 1 : 0;
+}
+
+// Kernel of a temporally blocked pass of k steps for the requested kind
+// (0 automatic, 1 row wavefronts, 2 tiles): 1 or 2, the other one where the
+// requested kernel does not support the lattice, 0 if neither does (k = 1).
+int blocked_kind(const fhp_lattice* h, int k, int bk) {
+    if (k <= 1) return 0;
+    const bool wave = fhp::wave_supported(h->g, k), tiles = fhp::block_supported(h->g, k);
+    if (bk == 2) return tiles ? 2 : (wave ? 1 : 0);
+    return wave ? 1 : (tiles ? 2 : 0);
 }
 
 int check_block(fhp_lattice* h, int32_t B) {
@@ -422,8 +436,8 @@ int fhp_step(fhp_lattice* h, int64_t n) {
     if (n > kMaxTime - h->t) return fail(h, FHP_EINVAL, "step counter would pass 2^48");
     DeviceGuard dg(h->device);
     const fhp::Key2 key{(uint32_t)h->seed, (uint32_t)(h->seed >> 32)};
-    int kernel = h->step_kernel, k_block = h->k_block;
-    effective_settings(h, &kernel, &k_block);
+    int kernel = h->step_kernel, k_block = h->k_block, bk = h->block_kernel;
+    effective_settings(h, &kernel, &k_block, &bk);
     const int gh = resident_interval(h, kernel, k_block);
     if (gh > 0) {
         // The lattice stays in shared memory for launches of up to 2^24 steps
@@ -445,12 +459,19 @@ int fhp_step(fhp_lattice* h, int64_t n) {
         return FHP_OK;
     }
     if (kernel == fhp::kStepResident) kernel = fhp::kStepAuto;  // not supported for this lattice
-    if (k_block > 1 && fhp::block_supported(h->g, k_block)) {
-        // Temporal blocking: passes of k steps; the remainder one step at a time.
+    const int blocked = blocked_kind(h, k_block, bk);
+    if (blocked != 0) {
+        const bool wave = blocked == 1;
+        // Temporal blocking: passes of k steps (row wavefronts where the rows
+        // fit shared memory, else 2-D tiles); the remainder one step at a time.
         const int k = k_block;
         while (n >= k) {
-            cudaError_t e = fhp::launch_block(h->g, h->buf[h->cur], h->buf[h->cur ^ 1], h->solid, h->has_solid,
-                                              h->force, h->ft, key, (uint64_t)h->t, k, h->stream, h->flags + 1);
+            cudaError_t e = wave ? fhp::launch_wave(h->g, h->buf[h->cur], h->buf[h->cur ^ 1], h->solid,
+                                                    h->has_solid, h->force, h->ft, key, (uint64_t)h->t, k,
+                                                    h->stream, h->flags + 1)
+                                 : fhp::launch_block(h->g, h->buf[h->cur], h->buf[h->cur ^ 1], h->solid,
+                                                     h->has_solid, h->force, h->ft, key, (uint64_t)h->t, k,
+                                                     h->stream, h->flags + 1);
             if (e != cudaSuccess) return cuda_fail(h, e, "launching the temporally blocked kernel");
             ++h->launches;
             h->cur ^= 1;
@@ -545,7 +566,8 @@ int fhp_set_forcing(fhp_lattice* h, double p) {
 
 int fhp_set_temporal_block(fhp_lattice* h, int32_t k) {
     if (!h) return fail(nullptr, FHP_EINVAL, "lattice is NULL");
-    if (k != 1 && k != 2 && k != 4 && k != 8) return fail(h, FHP_EINVAL, "temporal block %d not in {1,2,4,8}", k);
+    if (k != 1 && k != 2 && k != 3 && k != 4 && k != 8)
+        return fail(h, FHP_EINVAL, "temporal block %d not in {1, 2, 3, 4, 8}", k);
     h->k_block = k;
     return FHP_OK;
 }
@@ -619,11 +641,26 @@ int fhp_set_rows_device(fhp_lattice* h, int32_t y0, int32_t n, const uint32_t* d
 
 int fhp_get_temporal_block(const fhp_lattice* h) {
     if (!h) return -1;
-    int kernel, k_block;
-    effective_settings(h, &kernel, &k_block);
+    int kernel, k_block, bk;
+    effective_settings(h, &kernel, &k_block, &bk);
     const int gh = resident_interval(h, kernel, k_block);
     if (gh > 0) return gh;
-    return k_block > 1 && fhp::block_supported(h->g, k_block) ? k_block : 1;
+    return blocked_kind(h, k_block, bk) != 0 ? k_block : 1;
+}
+
+int fhp_set_temporal_block_kernel(fhp_lattice* h, int32_t kind) {
+    if (!h) return fail(nullptr, FHP_EINVAL, "lattice is NULL");
+    if (kind < 0 || kind > 2) return fail(h, FHP_EINVAL, "temporal-block kernel %d not in {0, 1, 2}", kind);
+    h->block_kernel = kind;
+    return FHP_OK;
+}
+
+int fhp_get_temporal_block_kernel(const fhp_lattice* h) {
+    if (!h) return -1;
+    int kernel, k_block, bk;
+    effective_settings(h, &kernel, &k_block, &bk);
+    if (resident_interval(h, kernel, k_block) > 0) return 0;
+    return blocked_kind(h, k_block, bk);
 }
 
 int fhp_autotune(fhp_lattice* h, int32_t trial_steps, int32_t* out_kernel, int32_t* out_temporal_block) {
@@ -643,26 +680,33 @@ int fhp_autotune(fhp_lattice* h, int32_t trial_steps, int32_t* out_kernel, int32
     }
     const int cur0 = h->cur;
     const int64_t t0 = h->t;
-    const int kernel0 = h->step_kernel, k0 = h->k_block;
+    const int kernel0 = h->step_kernel, k0 = h->k_block, bk0 = h->block_kernel;
     e = cudaMemcpyAsync(saved, h->buf[cur0], state_bytes, cudaMemcpyDeviceToDevice, h->stream);
     cudaEvent_t ev[2] = {nullptr, nullptr};
     if (e == cudaSuccess) e = cudaEventCreate(&ev[0]);
     if (e == cudaSuccess) e = cudaEventCreate(&ev[1]);
     std::vector<TuneChoice> cands;
-    cands.push_back({fhp::kStepDirect, 1});
+    cands.push_back({fhp::kStepDirect, 1, 0});
     if (fhp::resolved_step_kernel(h->g, h->has_solid, fhp::kStepRing) != fhp::kStepDirect) {
-        cands.push_back({fhp::kStepRing, 1});
-        cands.push_back({fhp::kStepRun, 1});
+        cands.push_back({fhp::kStepRing, 1, 0});
+        cands.push_back({fhp::kStepRun, 1, 0});
     }
-    if (fhp::resident_supported(h->g, h->has_solid, h->staging_bytes, 1)) cands.push_back({fhp::kStepResident, 1});
-    if (fhp::resident_supported(h->g, h->has_solid, h->staging_bytes, 2)) cands.push_back({fhp::kStepResident, 2});
+    if (fhp::resident_supported(h->g, h->has_solid, h->staging_bytes, 1))
+        cands.push_back({fhp::kStepResident, 1, 0});
+    if (fhp::resident_supported(h->g, h->has_solid, h->staging_bytes, 2))
+        cands.push_back({fhp::kStepResident, 2, 0});
+    // Temporal blocks (trial_steps mod k steps run one at a time): row
+    // wavefronts and 2-D tiles, where each supports the lattice.
+    for (int k : {2, 3, 4})
+        if (fhp::wave_supported(h->g, k)) cands.push_back({fhp::kStepDirect, k, 1});
     for (int k : {2, 4, 8})
-        if (fhp::block_supported(h->g, k) && trial_steps % k == 0) cands.push_back({fhp::kStepDirect, k});
-    TuneChoice best{fhp::kStepDirect, 1};
+        if (fhp::block_supported(h->g, k)) cands.push_back({fhp::kStepDirect, k, 2});
+    TuneChoice best{fhp::kStepDirect, 1, 0};
     float best_ms = -1.0f;
     for (size_t i = 0; e == cudaSuccess && i < cands.size(); ++i) {
         h->step_kernel = cands[i].kernel;
         h->k_block = cands[i].k;
+        h->block_kernel = cands[i].bk;
         // One untimed trial (first-use set-up), then the timed one.
         rc = fhp_step(h, trial_steps);
         if (rc == FHP_OK) rc = fhp_synchronize(h);
@@ -705,6 +749,7 @@ int fhp_autotune(fhp_lattice* h, int32_t trial_steps, int32_t* out_kernel, int32
     if (rc != FHP_OK || e != cudaSuccess || best_ms < 0.0f) {
         h->step_kernel = kernel0;
         h->k_block = k0;
+        h->block_kernel = bk0;
         if (rc != FHP_OK) return rc;
         if (e != cudaSuccess) return cuda_fail(h, e, "autotuning");
         return fail(h, FHP_ECUDA, "autotune: no step configuration ran");
@@ -713,6 +758,7 @@ int fhp_autotune(fhp_lattice* h, int32_t trial_steps, int32_t* out_kernel, int32
     // shape (and obstacle / forcing flags) on this device.
     h->step_kernel = fhp::kStepAuto;
     h->k_block = 1;
+    h->block_kernel = 0;
     record_tuned(TuneKey{h->device, h->g.W, h->g.H, h->has_solid, h->force, h->g.rules}, best);
     if (out_kernel) *out_kernel = best.kernel;
     if (out_temporal_block) *out_temporal_block = best.k;

@@ -127,6 +127,16 @@ cudaError_t launch_block(const Geometry& g, const uint32_t* src, uint32_t* dst, 
                          bool has_solid, bool force, const ForcingTable& ft, Key2 key, uint64_t t0, int k,
                          cudaStream_t stream, unsigned int* err);
 
+// Temporal blocking by row wavefronts (fhp_wave.cu): k (2, 3 or 4) steps from
+// src (state at t0) to dst in one pass over full-width row bands, the
+// intermediate levels in shared-memory row rings.  Supported when a row of
+// every level ring fits shared memory (about W <= 16,384 for k = 2 and 3,
+// 8,192 for k = 4) and the rule set is FHP-I or FHP-II.
+bool wave_supported(const Geometry& g, int k);
+cudaError_t launch_wave(const Geometry& g, const uint32_t* src, uint32_t* dst, const uint32_t* solid,
+                        bool has_solid, bool force, const ForcingTable& ft, Key2 key, uint64_t t0, int k,
+                        cudaStream_t stream, unsigned int* err);
+
 // Pack H x W node bytes (device) into 7 state planes + the solid plane.
 // Sets *device_any_solid to a nonzero value if any node is solid.
 cudaError_t launch_pack(const Geometry& g, const uint8_t* bytes, uint32_t* state,

@@ -87,6 +87,8 @@ def load(path: str | None = None):
         "fhp_set_time": (ctypes.c_int, [vp, i64]),
         "fhp_set_forcing": (ctypes.c_int, [vp, ctypes.c_double]),
         "fhp_set_temporal_block": (ctypes.c_int, [vp, i32]),
+        "fhp_set_temporal_block_kernel": (ctypes.c_int, [vp, i32]),
+        "fhp_get_temporal_block_kernel": (ctypes.c_int, [vp]),
         "fhp_synchronize": (ctypes.c_int, [vp]),
         "fhp_set_step_kernel": (ctypes.c_int, [vp, i32]),
         "fhp_get_step_kernel": (ctypes.c_int, [vp]),
@@ -277,6 +279,15 @@ class Lattice:
 
     def set_temporal_block(self, k: int):
         self._check(self._lib.fhp_set_temporal_block(self._h, int(k)))
+
+    def set_temporal_block_kernel(self, kind: int):
+        """0: automatic; 1: row wavefronts; 2: 2-D tiles (see fhp.h)."""
+        self._check(self._lib.fhp_set_temporal_block_kernel(self._h, int(kind)))
+
+    @property
+    def temporal_block_kernel(self) -> int:
+        """Kernel of the blocked passes fhp_step runs: 1 wavefronts, 2 tiles, 0 none."""
+        return int(self._lib.fhp_get_temporal_block_kernel(self._h))
 
     def set_step_kernel(self, kind: int):
         """0 automatic, 1 direct register loads, 2 bulk-copy shared-memory ring, 3 multi-step ring,

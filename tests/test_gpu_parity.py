@@ -27,11 +27,14 @@ def fhp_mod():
     return pkg
 
 
-def gpu_run(pkg, s0, seed, t0, n, p, chunks=None, kernel=0, k_block=1):
+def gpu_run(pkg, s0, seed, t0, n, p, chunks=None, kernel=0, k_block=1, bk=0):
     H, W = s0.shape
     with pkg.Lattice(W, H, seed=seed, forcing_p=p, step_kernel=kernel) as lat:
         lat.set_temporal_block(k_block)
+        lat.set_temporal_block_kernel(bk)
         lat.set_state(s0)
+        if bk and k_block > 1:
+            assert lat.temporal_block_kernel == bk, "the requested temporal-block kernel must run"
         lat.set_time(t0)
         for c in (chunks or [n]):
             lat.step(c)
@@ -114,13 +117,17 @@ def test_parity_ring_many_tiles(fhp_mod, oracle_mod, W, H, kernel):
     assert_same(got, want, f"kernel {kernel} {W}x{H}")
 
 
-@pytest.mark.parametrize("k", [2, 4, 8])
+# (temporal block k, its kernel): row wavefronts (1) for k = 2, 3, 4; 2-D tiles (2) for k = 2, 4, 8
+BLOCKS = [(2, 1), (3, 1), (4, 1), (2, 2), (4, 2), (8, 2)]
+
+
+@pytest.mark.parametrize("k,bk", BLOCKS)
 @pytest.mark.parametrize("W,H", [(512, 18), (640, 46), (4224, 100), (2048, 512), (4096, 1030)])
 @pytest.mark.parametrize("variant", ["periodic", "walls_forcing", "points_forcing"])
-def test_parity_temporal_block(fhp_mod, oracle_mod, W, H, k, variant):
-    """k steps per pass in shared memory (2-D tiles with a k-row / 128-node
-    halo, periodic wrap of the halo in x and y): bit-exact for passes plus a
-    remainder of single steps."""
+def test_parity_temporal_block(fhp_mod, oracle_mod, W, H, k, bk, variant):
+    """k steps per pass on chip (row wavefronts through per-level row rings,
+    or 2-D tiles with a k-row / 128-node halo; periodic wrap in x and y):
+    bit-exact for passes plus a remainder of single steps."""
     seed = 77 + W + H + k
     rng = np.random.Generator(np.random.PCG64(seed))
     if variant == "periodic":
@@ -132,8 +139,40 @@ def test_parity_temporal_block(fhp_mod, oracle_mod, W, H, k, variant):
     s0 = workloads.bernoulli_lattice(W, H, 0.35, seed, solid)
     steps = 2 * k + 3
     want, _ = oracle_mod.run(s0, seed, 5, steps, p)
-    got = gpu_run(fhp_mod, s0, seed, 5, steps, p, k_block=k)
-    assert_same(got, want, f"{W}x{H} {variant} k={k}")
+    got = gpu_run(fhp_mod, s0, seed, 5, steps, p, k_block=k, bk=bk)
+    assert_same(got, want, f"{W}x{H} {variant} k={k} kernel {bk}")
+
+
+# Row-wavefront shapes: 1 to 4 columns of 32 quads (one to four warps per
+# level row), ragged last quads, lattices lower than a band's halo (rows wrap
+# more than once), and the widest rows each k supports.
+WAVE_SHAPES = [(32, 2), (32, 6), (96, 4), (128, 10), (1024, 16), (4096, 12), (4128, 8), (8192 + 96, 6),
+               (12288, 4), (16384, 8), (256, 2048)]
+
+
+@pytest.mark.parametrize("k", [2, 3, 4])
+@pytest.mark.parametrize("W,H", WAVE_SHAPES)
+@pytest.mark.parametrize("variant", ["periodic", "walls_forcing", "points_forcing"])
+def test_parity_wavefront_shapes(fhp_mod, oracle_mod, W, H, k, variant):
+    seed = 31 + 3 * W + H + k
+    rng = np.random.Generator(np.random.PCG64(seed))
+    if variant == "periodic":
+        solid, p = None, 0.0
+    elif variant == "walls_forcing":
+        solid, p = workloads.channel_walls(W, H), 0.05
+    else:
+        solid, p = workloads.random_points(W, H, 0.05, rng), 0.3
+    s0 = workloads.bernoulli_lattice(W, H, 0.35, seed, solid)
+    steps = 2 * k + 1
+    want, _ = oracle_mod.run(s0, seed, 7, steps, p)
+    with fhp_mod.Lattice(W, H, seed=seed, forcing_p=p) as lat:
+        lat.set_temporal_block(k)
+        lat.set_temporal_block_kernel(1)
+        lat.set_state(s0)
+        assert lat.temporal_block == k and lat.temporal_block_kernel == 1
+        lat.set_time(7)
+        lat.step(steps)
+        assert_same(lat.get_state(), want, f"{W}x{H} {variant} wavefront k={k}")
 
 
 @pytest.mark.parametrize("k", [4, 8])
@@ -148,18 +187,19 @@ def test_temporal_block_forcing_near_tile_edges(fhp_mod, oracle_mod, k):
         s0 = workloads.bernoulli_lattice(W, H, 0.35, seed, workloads.random_points(W, H, 0.05, rng))
         for p in (0.2, 0.5):
             want, _ = oracle_mod.run(s0, seed, 5, k, p)
-            got = gpu_run(fhp_mod, s0, seed, 5, k, p, k_block=k)
+            got = gpu_run(fhp_mod, s0, seed, 5, k, p, k_block=k, bk=2)
             assert_same(got, want, f"seed {seed} p {p} k {k}")
 
 
 def test_temporal_block_full_size_all_k(fhp_mod, oracle_mod):
-    """16384 x 4096 cylinder: 24 steps give the same state for k = 1, 2, 4, 8
-    and equal the oracle."""
+    """16384 x 4096 cylinder: 24 steps give the same state for k = 1 and every
+    blocked kernel and k, and equal the oracle."""
     job = workloads.cylinder_16384x4096()
     s0 = job.initial_state()
     want, _ = oracle_mod.run(s0, job.seed, 0, 24, job.p)
-    for k in (1, 2, 4, 8):
-        assert_same(gpu_run(fhp_mod, s0, job.seed, 0, 24, job.p, k_block=k), want, f"k={k}")
+    assert_same(gpu_run(fhp_mod, s0, job.seed, 0, 24, job.p), want, "k=1")
+    for k, bk in BLOCKS:
+        assert_same(gpu_run(fhp_mod, s0, job.seed, 0, 24, job.p, k_block=k, bk=bk), want, f"k={k} kernel {bk}")
 
 
 def test_cylinder_1000_steps_same_for_every_k(fhp_mod):
@@ -169,8 +209,9 @@ def test_cylinder_1000_steps_same_for_every_k(fhp_mod):
     job = workloads.cylinder_16384x4096()
     s0 = job.initial_state()
     ref = gpu_run(fhp_mod, s0, job.seed, 0, job.steps, job.p)
-    for k in (2, 4, 8):
-        assert_same(gpu_run(fhp_mod, s0, job.seed, 0, job.steps, job.p, k_block=k), ref, f"1000 steps, k={k}")
+    for k, bk in BLOCKS:
+        assert_same(gpu_run(fhp_mod, s0, job.seed, 0, job.steps, job.p, k_block=k, bk=bk), ref,
+                    f"1000 steps, k={k} kernel {bk}")
     assert_same(gpu_run(fhp_mod, s0, job.seed, 0, job.steps, job.p, kernel=2), ref, "1000 steps, ring")
 
 
