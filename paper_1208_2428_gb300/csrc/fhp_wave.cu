@@ -265,6 +265,8 @@ __global__ void __launch_bounds__(kWaveThreads, 1) fhp_wave_kernel(const StepArg
                 }
                 // Output slot: its old row i - D is read by level j+1 rows i-D-2 .. i-D.
                 if (ok && j < K) ok = wait_rows(done + (j + 1) * C * P, c, C, P, i - wa.D);
+                // A wait that gave up in one lane ends the warp's loop in all of them.
+                ok = __all_sync(0xFFFFFFFFu, ok);
                 if (!ok) break;
                 if (active) {
                     if (j == K) {
