@@ -685,26 +685,25 @@ def run_gpu(args):
 
 def temporal_block_sweep(job, s0, seed, dev, stream, nsteps, peak):
     """One call of `nsteps` lattice steps from the same state for temporal
-    blocks k = 1, 2, 3, 4, 8 (k = 1: the automatic single-step choice; k > 1:
-    the automatic blocked kernel -- row wavefronts where they support the
-    lattice, else 2-D tiles -- and, as ``k<k>_tiles``, the 2-D tile kernel
-    where both exist): GSUPS, the HBM fraction of the algorithmic bytes (a
-    blocked pass reads and writes the state once per k steps) and whether the
-    final states are identical."""
+    blocks k = 1, 2, 4, 8 (k = 1: the automatic single-step choice; k > 1:
+    the automatic blocked kernel, 2-D tiles where they apply) and, as
+    ``k<k>_wave``, the row-wavefront kernel for k = 2, 3, 4: GSUPS, the HBM
+    fraction of the algorithmic bytes (a blocked pass reads and writes the
+    state once per k steps) and whether the final states are identical."""
     import numpy as np
     import torch
     from paper_1208_2428_gb300 import Lattice
     bytes_per_node = (14 + (1 if (s0 & 0x80).any() else 0)) / 8.0
     names = {0: None, 1: "fhp_wave_kernel", 2: "fhp_block_kernel"}
     out, ref = {}, None
-    for k, bk in ((1, 0), (2, 0), (3, 0), (4, 0), (8, 0), (2, 2), (4, 2)):
+    for k, bk in ((1, 0), (2, 0), (4, 0), (8, 0), (2, 1), (3, 1), (4, 1)):
         with Lattice(job.W, job.H, seed=seed, forcing_p=job.p, device=dev, stream=stream) as lat:
             lat.set_step_kernel(0)
             lat.set_temporal_block(k)
             lat.set_temporal_block_kernel(bk)
             used_k, used_bk = lat.temporal_block, lat.temporal_block_kernel
             if bk and used_bk != bk:
-                continue               # the tile kernel does not apply: already covered by the automatic line
+                continue               # the requested kernel does not apply here
             lat.set_state(s0)
             lat.step(64)
             lat.set_state(s0)
@@ -720,9 +719,9 @@ def temporal_block_sweep(job, s0, seed, dev, stream, nsteps, peak):
         if ref is None:
             ref = final
         gsups = job.W * job.H * nsteps / (ms / 1e3) / 1e9
-        key = f"k{k}" + ("_tiles" if bk == 2 else "")
-        if bk == 2 and out.get(f"k{k}", {}).get("kernel") == names[2]:
-            continue                   # the automatic line already ran the tile kernel
+        key = f"k{k}" + ("_wave" if bk == 1 else "")
+        if bk == 1 and out.get(f"k{k}", {}).get("kernel") == names[1]:
+            continue                   # the automatic line already ran the wavefront kernel
         out[key] = {"temporal_block": used_k, "kernel": names.get(used_bk) or "single-step (automatic)",
                     "gsups": gsups, "ms": ms,
                     "hbm_frac": gsups * 1e9 * bytes_per_node / used_k / (peak * 1e9),

@@ -154,7 +154,8 @@ FHP_API int fhp_set_forcing(fhp_lattice* lattice, double p);
 
 /* Number of steps fused into one kernel pass (temporal blocking): 1, 2, 3,
  * 4 or 8.  With k > 1, fhp_step runs passes that read the state from HBM
- * once, apply k steps on chip and write the result once.  Two kernels do it:
+ * once, apply k steps on chip and write the result once.  Two kernels do it
+ * (fhp_set_temporal_block_kernel chooses):
  *  - row wavefronts (k = 2, 3, 4) where a full row of every intermediate time
  *    level fits shared memory (FHP-I/II lattices up to about 16,384 nodes per
  *    row for k = 2 and 3, about 8,192 for k = 4): each CTA streams a band of
@@ -237,8 +238,8 @@ FHP_API int fhp_set_rows_device(fhp_lattice* lattice, int32_t y0, int32_t n, con
  * -1 for a NULL lattice. */
 FHP_API int fhp_get_temporal_block(const fhp_lattice* lattice);
 
-/* Kernel of the temporally blocked passes: 0 = automatic (row wavefronts
- * where they support the lattice, else 2-D tiles; default), 1 = row
+/* Kernel of the temporally blocked passes: 0 = automatic (2-D tiles where
+ * they support the lattice and k, else row wavefronts; default), 1 = row
  * wavefronts, 2 = 2-D tiles; a kernel that does not support the lattice or k
  * falls back to the other one.  Results are identical for every choice.
  * FHP_EINVAL for other values.  fhp_get_temporal_block_kernel returns the

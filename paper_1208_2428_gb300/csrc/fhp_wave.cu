@@ -68,9 +68,9 @@ __device__ __forceinline__ unsigned int rows_upto(int m, int p, int P) {
     return m < p ? 0u : (unsigned int)((m - p) / P + 1);
 }
 
-__device__ __forceinline__ unsigned int ld_acquire_shared(const unsigned int* p) {
+__device__ __forceinline__ unsigned int ld_relaxed_shared(const unsigned int* p) {
     unsigned int v;
-    asm volatile("ld.acquire.cta.shared::cta.u32 %0, [%1];" : "=r"(v) : "r"(smem_addr(p)) : "memory");
+    asm volatile("ld.relaxed.cta.shared::cta.u32 %0, [%1];" : "=r"(v) : "r"(smem_addr(p)) : "memory");
     return v;
 }
 
@@ -78,36 +78,53 @@ __device__ __forceinline__ void st_release_shared(unsigned int* p, unsigned int 
     asm volatile("st.release.cta.shared::cta.u32 [%0], %1;" ::"r"(smem_addr(p)), "r"(v) : "memory");
 }
 
-// Wait until, in the columns c-1, c, c+1 (periodic) of one level, the rows of
-// index 0..m of every parity are finished.  Every lane polls (the counters
-// are read with acquire by each lane that then reads the rows).  Returns
-// false after kWaitLimitNs.
-__device__ __forceinline__ bool wait_rows(const unsigned int* level_done, int c, int C, int P, int m) {
-    if (m < 0) return true;
-    const int cl = c == 0 ? C - 1 : c - 1, cr = c == C - 1 ? 0 : c + 1;
-    unsigned long long start = 0;
-    for (;;) {
-        bool ok = true;
-        for (int p = 0; p < P; ++p) {
-            const unsigned int need = rows_upto(m, p, P);
-            ok = ok && ld_acquire_shared(level_done + c * P + p) >= need;
-            ok = ok && ld_acquire_shared(level_done + cl * P + p) >= need;
-            ok = ok && ld_acquire_shared(level_done + cr * P + p) >= need;
+// Wait until, in the columns c-1, c, c+1 (periodic) of one level's counters,
+// the rows of index 0..m of every parity are counted.  Lane 0 polls with
+// relaxed loads and then takes one CTA-scope fence (acquire); __syncwarp
+// orders the other lanes' later reads after it.  Warp-uniform result; false
+// after kWaitLimitNs.
+__device__ __forceinline__ bool wait_rows(const unsigned int* level, int c, int C, int P, int m, int lane) {
+    int ok = 1;
+    if (m >= 0 && lane == 0) {
+        const int cl = c == 0 ? C - 1 : c - 1, cr = c == C - 1 ? 0 : c + 1;
+        unsigned long long start = 0;
+        for (;;) {
+            bool ready = true;
+            for (int p = 0; p < P; ++p) {
+                const unsigned int need = rows_upto(m, p, P);
+                ready = ready && ld_relaxed_shared(level + c * P + p) >= need &&
+                        ld_relaxed_shared(level + cl * P + p) >= need &&
+                        ld_relaxed_shared(level + cr * P + p) >= need;
+            }
+            if (ready) break;
+            const unsigned long long now = global_ns();
+            if (start == 0) start = now;
+            else if (now - start > kWaitLimitNs) {
+                ok = 0;
+                break;
+            }
+            __nanosleep(64);   // leave the issue slots to the warps that compute
         }
-        if (ok) return true;
-        const unsigned long long now = global_ns();
-        if (start == 0) start = now;
-        else if (now - start > kWaitLimitNs) return false;
+        __threadfence_block();
     }
+    ok = __shfl_sync(0xFFFFFFFFu, ok, 0);
+    __syncwarp();
+    return ok != 0;
 }
 
-// One quad of a level row.  rm, r0, rp: rows y-1, y, y+1 of the previous
-// level (planes Pq words apart); sd: solid words of row y (shared or global
-// memory); LAST stores to global memory, else into `out` (a level slot).
-template <bool SOLID, bool FORCE, bool RAGGED, bool LAST>
-__device__ __forceinline__ void wave_quad(const StepArgs& a, const StepVar& v, const uint32_t* rm,
-                                          const uint32_t* r0, const uint32_t* rp, const uint32_t* sd_row,
-                                          bool sd_global, uint32_t* out, int y, int q) {
+// The inputs of one quad of a level row: the quad's words of the seven
+// planes of rows y-1, y, y+1 of the previous level (planes Pq words apart),
+// already shifted by the motion step, and its solid words.
+struct QuadIn {
+    uint4 n0, n1, n2, n3, n4, n5, i6, sd;
+};
+
+// Shared-memory reads only (the solid words of a level-1 row come with the
+// staged row; the other levels read theirs from global memory in wave_finish,
+// after the quad has released its input rows).
+template <bool SOLID, bool RAGGED>
+__device__ __forceinline__ QuadIn wave_load(const StepArgs& a, const uint32_t* rm, const uint32_t* r0,
+                                            const uint32_t* rp, const uint32_t* sd_smem, int y, int q) {
     const int Pq = a.Pq;
     const int w = 4 * q;
     const int m = RAGGED ? (q == a.nq - 1 ? a.Wq - w : 4) : 4;
@@ -115,42 +132,55 @@ __device__ __forceinline__ void wave_quad(const StepArgs& a, const StepVar& v, c
     const int wr = q == a.nq - 1 ? 0 : w + 4;       // word right of the quad (periodic)
     const uint4 i3 = ld4(rm + 3 * Pq + w), i4 = ld4(rm + 4 * Pq + w);
     const uint4 i2 = ld4(r0 + 2 * Pq + w), i5 = ld4(r0 + 5 * Pq + w);
-    const uint4 i6 = ld4(r0 + 6 * Pq + w);
     const uint4 i0 = ld4(rp + 0 * Pq + w), i1 = ld4(rp + 1 * Pq + w);
-    uint4 sd = make_uint4(0u, 0u, 0u, 0u);
-    if (SOLID) sd = sd_global ? __ldg(reinterpret_cast<const uint4*>(sd_row + w)) : ld4(sd_row + w);
-    uint4 n0, n1, n2, n3, n4, n5;
+    QuadIn in;
+    in.i6 = ld4(r0 + 6 * Pq + w);
+    in.sd = make_uint4(0u, 0u, 0u, 0u);
+    if (SOLID && sd_smem) in.sd = ld4(sd_smem + w);
     if ((y & 1) == 0) {
         // Even row: E, NE, SE come from x-1; W from x+1; NW, SW from x.
-        n2 = pull_left(i2, r0[2 * Pq + wl]);
-        n3 = pull_left(i3, rm[3 * Pq + wl]);
-        n1 = pull_left(i1, rp[1 * Pq + wl]);
-        n5 = pull_right<RAGGED>(i5, r0[5 * Pq + wr], m);
-        n4 = i4;
-        n0 = i0;
+        in.n2 = pull_left(i2, r0[2 * Pq + wl]);
+        in.n3 = pull_left(i3, rm[3 * Pq + wl]);
+        in.n1 = pull_left(i1, rp[1 * Pq + wl]);
+        in.n5 = pull_right<RAGGED>(i5, r0[5 * Pq + wr], m);
+        in.n4 = i4;
+        in.n0 = i0;
     } else {
         // Odd row: E from x-1; W, NW, SW from x+1; NE, SE from x.
-        n2 = pull_left(i2, r0[2 * Pq + wl]);
-        n5 = pull_right<RAGGED>(i5, r0[5 * Pq + wr], m);
-        n4 = pull_right<RAGGED>(i4, rm[4 * Pq + wr], m);
-        n0 = pull_right<RAGGED>(i0, rp[0 * Pq + wr], m);
-        n3 = i3;
-        n1 = i1;
+        in.n2 = pull_left(i2, r0[2 * Pq + wl]);
+        in.n5 = pull_right<RAGGED>(i5, r0[5 * Pq + wr], m);
+        in.n4 = pull_right<RAGGED>(i4, rm[4 * Pq + wr], m);
+        in.n0 = pull_right<RAGGED>(i0, rp[0 * Pq + wr], m);
+        in.n3 = i3;
+        in.n1 = i1;
     }
+    return in;
+}
+
+// Scattering, bounce-back and forcing of the quad; LAST stores the result to
+// global memory, else into `out` (a level slot).
+template <bool SOLID, bool FORCE, bool RAGGED>
+__device__ __forceinline__ void wave_finish(const StepArgs& a, const StepVar& v, const QuadIn& in,
+                                            const uint32_t* sd_global, uint32_t* out, bool last, int y, int q) {
+    uint4 sd = in.sd;
+    if (SOLID && sd_global) sd = __ldg(reinterpret_cast<const uint4*>(sd_global + 4 * q));
     uint4 o[7];
-    collide_quad<SOLID, FORCE>(a, v, q, y, n0, n1, n2, n3, n4, n5, i6, sd, o);
-    if (LAST) {
+    collide_quad<SOLID, FORCE>(a, v, q, y, in.n0, in.n1, in.n2, in.n3, in.n4, in.n5, in.i6, sd, o);
+    if (last) {
+        const int m = RAGGED ? (q == a.nq - 1 ? a.Wq - 4 * q : 4) : 4;
         store_quad<RAGGED>(a, v.dst, q, y, m, o);
     } else {
 #pragma unroll
-        for (int k = 0; k < 7; ++k) st4(out + k * Pq + w, o[k]);
+        for (int k = 0; k < 7; ++k) st4(out + k * a.Pq + 4 * q, o[k]);
     }
 }
 
 template <int K, bool SOLID, bool FORCE, bool RAGGED>
 __global__ void __launch_bounds__(kWaveThreads, 1) fhp_wave_kernel(const StepArgs a, const WaveArgs wa) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    unsigned int* done = reinterpret_cast<unsigned int*>(smem_raw);                   // [K+1][C][P]
+    // Row counters: rd[j] counts rows of level j whose inputs have been read,
+    // wr[j] rows of level j written to its ring (per column and parity).
+    unsigned int* rd = reinterpret_cast<unsigned int*>(smem_raw);                     // [K+1][C][P]
     uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw + kWaveCounterBytes);         // [D0]
     uint32_t* ring0 = reinterpret_cast<uint32_t*>(smem_raw + kWaveHeaderBytes);        // D0 x 8 planes
     const int Pq = a.Pq;
@@ -159,6 +189,7 @@ __global__ void __launch_bounds__(kWaveThreads, 1) fhp_wave_kernel(const StepArg
     uint32_t* ring = ring0 + (size_t)wa.D0 * slot0_words;                               // (K-1) x D x 7 planes
     const int C = wa.C, P = wa.P;
     const int ncomp = K * C * P;
+    unsigned int* wr = rd + (K + 1) * C * P;                                            // [K+1][C][P]
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     __shared__ int abort_flag;
 
@@ -167,7 +198,7 @@ __global__ void __launch_bounds__(kWaveThreads, 1) fhp_wave_kernel(const StepArg
         const int y0 = (int)(((long long)band * a.H) / wa.nbands);
         const int y1 = (int)(((long long)(band + 1) * a.H) / wa.nbands);
         const int B = y1 - y0;
-        for (int i = threadIdx.x; i < (K + 1) * C * P; i += blockDim.x) done[i] = 0;
+        for (int i = threadIdx.x; i < 2 * (K + 1) * C * P; i += blockDim.x) rd[i] = 0;
         if (threadIdx.x == 0) {
             for (int s = 0; s < wa.D0; ++s) mbar_init(&full[s], 1);
             asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -187,14 +218,14 @@ __global__ void __launch_bounds__(kWaveThreads, 1) fhp_wave_kernel(const StepArg
                     const int s = i % wa.D0;
                     if (i >= wa.D0) {
                         // The slot's old row i - D0 is read by level-1 rows i-D0-2 .. i-D0.
-                        const unsigned int* lv1 = done + 1 * C * P;
+                        const unsigned int* lv1 = rd + 1 * C * P;
                         const int m = i - wa.D0;
                         unsigned long long start = 0;
                         for (;;) {
                             bool ready = true;
                             for (int c = 0; c < C && ready; ++c)
                                 for (int p = 0; p < P && ready; ++p)
-                                    ready = ld_acquire_shared(lv1 + c * P + p) >= rows_upto(m, p, P);
+                                    ready = ld_relaxed_shared(lv1 + c * P + p) >= rows_upto(m, p, P);
                             if (ready) break;
                             const unsigned long long now = global_ns();
                             if (start == 0) start = now;
@@ -202,8 +233,10 @@ __global__ void __launch_bounds__(kWaveThreads, 1) fhp_wave_kernel(const StepArg
                                 ok = false;
                                 break;
                             }
+                            __nanosleep(64);
                         }
                         if (!ok) break;
+                        __threadfence_block();   // acquire: the readers are done with the slot
                     }
                     const int y = wrap_row(y0 - K + i, a.H);
                     uint32_t* dst = ring0 + (size_t)s * slot0_words;
@@ -240,45 +273,51 @@ __global__ void __launch_bounds__(kWaveThreads, 1) fhp_wave_kernel(const StepArg
             bool ok = true;
             for (int i = p; i < nj; i += P) {
                 // Inputs: rows i, i+1, i+2 of level j-1 (lattice rows y-1, y, y+1).
-                const uint32_t *rm, *r0, *rp, *sd_row;
-                bool sd_global;
+                const uint32_t *rm, *r0, *rp, *sd_smem, *sd_global;
                 const int y = wrap_row(start + i, a.H);
                 if (j == 1) {
                     // Every row's slot phase is waited for in row order (the
                     // first iteration also covers the rows below it), so a
                     // slot's previous use has completed before its next one
                     // is tested and the phase parity cannot alias.
-                    for (int r = (i == p ? 0 : i); r <= i + 2 && ok; ++r)
-                        ok = mbar_wait_bounded(&full[r % wa.D0], (uint32_t)((r / wa.D0) & 1));
+                    for (int r = (i == p ? 0 : i); r <= i + 2 && ok; ++r) {
+                        const uint32_t par = (uint32_t)((r / wa.D0) & 1);
+                        if (!mbar_try_wait(&full[r % wa.D0], par)) ok = mbar_wait_bounded(&full[r % wa.D0], par);
+                    }
+                    ok = __all_sync(0xFFFFFFFFu, ok);
                     rm = ring0 + (size_t)(i % wa.D0) * slot0_words;
                     r0 = ring0 + (size_t)((i + 1) % wa.D0) * slot0_words;
                     rp = ring0 + (size_t)((i + 2) % wa.D0) * slot0_words;
-                    sd_row = r0 + 7 * (size_t)Pq;
-                    sd_global = false;
+                    sd_smem = r0 + 7 * (size_t)Pq;
+                    sd_global = nullptr;
                 } else {
-                    ok = wait_rows(done + (j - 1) * C * P, c, C, P, i + 2);
+                    ok = wait_rows(wr + (j - 1) * C * P, c, C, P, i + 2, lane);
                     rm = prev_ring + (size_t)(i % wa.D) * slot_words;
                     r0 = prev_ring + (size_t)((i + 1) % wa.D) * slot_words;
                     rp = prev_ring + (size_t)((i + 2) % wa.D) * slot_words;
-                    sd_row = a.solid + (size_t)y * Pq;
-                    sd_global = true;
+                    sd_smem = nullptr;
+                    sd_global = a.solid + (size_t)y * Pq;
                 }
                 // Output slot: its old row i - D is read by level j+1 rows i-D-2 .. i-D.
-                if (ok && j < K) ok = wait_rows(done + (j + 1) * C * P, c, C, P, i - wa.D);
-                // A wait that gave up in one lane ends the warp's loop in all of them.
-                ok = __all_sync(0xFFFFFFFFu, ok);
+                if (ok && j < K) ok = wait_rows(rd + (j + 1) * C * P, c, C, P, i - wa.D, lane);
                 if (!ok) break;
-                if (active) {
-                    if (j == K) {
-                        wave_quad<SOLID, FORCE, RAGGED, true>(a, v, rm, r0, rp, sd_row, sd_global, nullptr, y, q);
-                    } else {
-                        wave_quad<SOLID, FORCE, RAGGED, false>(a, v, rm, r0, rp, sd_row, sd_global,
-                                                               my_ring + (size_t)(i % wa.D) * slot_words, y, q);
-                    }
-                }
-                __threadfence_block();
+                const unsigned int count = (unsigned int)(i / P + 1);
+                QuadIn in;
+                if (active) in = wave_load<SOLID, RAGGED>(a, rm, r0, rp, sd_smem, y, q);
+                // The inputs are in registers: the level below may reuse their slots.
                 __syncwarp();
-                if (lane == 0) st_release_shared(done + j * C * P + c * P + p, (unsigned int)(i / P + 1));
+                if (lane == 0) st_release_shared(rd + j * C * P + c * P + p, count);
+                if (active) {
+                    // One copy of the collision code serves every level (the
+                    // store target is a warp-uniform choice).
+                    wave_finish<SOLID, FORCE, RAGGED>(a, v, in, sd_global,
+                                                      j < K ? my_ring + (size_t)(i % wa.D) * slot_words : nullptr,
+                                                      j == K, y, q);
+                }
+                if (j < K) {
+                    __syncwarp();
+                    if (lane == 0) st_release_shared(wr + j * C * P + c * P + p, count);
+                }
             }
             if (!ok && lane == 0) {
                 if (a.err) atomicOr(a.err, 1u);
