@@ -265,11 +265,12 @@ def batched_vs_per_lattice(dev, stream, count: int, steps: int, per_steps: int, 
         for j, s0 in zip(jobs, states):
             k = b.add(j.W, j.H, j.seed, j.p)
             b.set_state(k, s0)
-        b.step(128)  # warm-up; the automatic choice times both batch kernels here (64 steps each)
+        b.step(256)  # warm-up; the automatic choice times both kernels at two tile sizes here (64 steps each)
         b.synchronize()
         b.step(1)   # reads that measurement
         b.synchronize()
         tuned = b.tuned_kernel()
+        tuned_quads = b.tile_quads
         best = None
         for _ in range(repeats):
             l0 = b.kernel_launches
@@ -302,6 +303,9 @@ def batched_vs_per_lattice(dev, stream, count: int, steps: int, per_steps: int, 
     per = nodes * per_steps / (ms_per / 1e3) / 1e9
     return {"lattices": count, "nodes": nodes, "batched_gsups": batched, "batched_steps": steps,
             "batched_kernel": "fhp_batch_run_kernel" if tuned == 2 else "fhp_batch_kernel",
+            "batched_tile_quads": tuned_quads,
+            "tuned": {"kernel": tuned, "tile_quads": tuned_quads, "graph_steps": 64,
+                      "candidates": "single-step graphs / multi-step cooperative x 256 / 128 quads per tile"},
             "batched_launches": launches_batched, "per_lattice_gsups": per, "per_lattice_steps": per_steps,
             "per_lattice_launches": launches_per, "speedup": batched / per,
             "batched_ms": best, "per_lattice_ms": ms_per}
@@ -328,7 +332,7 @@ def run_ensemble(args):
         "vs_baseline": None, "dtype": "u32 (bit-planes, boolean/integer)",
         "data": "synthetic (512 seeded lattices, sides uniform in 128..2048 step 64, 1 % point obstacles)",
         "config": {"workload": f"ensemble_{args.ensemble_size}", "lattice_steps_per_step": steps,
-                   "graph_steps": 64, "l2": "inputs (1.1 GB) larger than L2"},
+                   "graph_steps": 64, "tuned": r["tuned"], "l2": "inputs (1.1 GB) larger than L2"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": None, "kernel": r["batched_kernel"], "algorithmic_bytes_per_node_step": bytes_per_node,
                      "peak_source": peak_src},

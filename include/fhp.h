@@ -50,6 +50,7 @@ extern "C" {
 #define FHP_ECUDA 3    /* a CUDA runtime call failed */
 #define FHP_ETIMEOUT 4 /* a bounded device-side wait gave up */
 #define FHP_EBUSY 5    /* the object is in use */
+#define FHP_EDEBUG 6   /* debug build: an index check failed (the access was skipped) */
 
 typedef struct fhp_lattice fhp_lattice;
 
@@ -304,6 +305,7 @@ FHP_API int64_t fhp_kernel_launches(const fhp_lattice* lattice);
  * when the timeout path works).  The device stays usable afterwards. */
 FHP_API int fhp_selftest_wait_limits(uint32_t* host_status);
 
+
 /* Diagnostic: Philox4x32-10 (Salmon et al., SC'11) evaluated by the
  * library's device code.  device_ctr holds n counters of 4 words,
  * device_key n keys of 2 words, device_out receives n blocks of 4 words.
@@ -388,22 +390,36 @@ FHP_API int fhp_batch_step(fhp_batch* batch, int64_t n);
  * MULTI_STEP: all steps of an fhp_batch_step call in one cooperative launch;
  * a tile is staged for step s once the tiles of step s - 1 it reads (itself
  * and its two neighbours in its lattice) are finished, tracked by per-tile
- * counters.  AUTO (default): autotuned online -- batches are classed by the
- * binary order of magnitude of their tile count (fhp_batch_tile_count); the
- * first call in a class of at least 2 * max(16, graph steps) steps runs half
- * of its steps with each kernel, timed with CUDA events on the batch's
- * stream, and a later call
- * records the kernel with more node updates per millisecond for the class
- * (read without waiting); until then SINGLE_STEP runs.  Results are
- * identical for every choice. */
+ * counters.  AUTO (default): autotuned online together with the tile size
+ * -- batches are classed by the binary order of magnitude of their tile
+ * count at the default size of 256 quads (128-node units) per tile; the
+ * first call in a class of at least c * max(16, graph steps) steps runs an
+ * equal part of its steps with each of c candidates -- both kernels, and,
+ * while the tile size is automatic (fhp_batch_set_tile_quads), tiles of 256
+ * and of 128 quads (c = 4; else c = 2) -- timed with CUDA events on the
+ * batch's stream, and a later call records the candidate with the most node
+ * updates per millisecond for the class (read without waiting); until then
+ * SINGLE_STEP with 256-quad tiles runs.  Results are identical for every
+ * choice. */
 #define FHP_BATCH_KERNEL_AUTO 0
 #define FHP_BATCH_KERNEL_SINGLE_STEP 1
 #define FHP_BATCH_KERNEL_MULTI_STEP 2
 FHP_API int fhp_batch_set_step_kernel(fhp_batch* batch, int32_t kind);
 FHP_API int fhp_batch_get_step_kernel(const fhp_batch* batch);
-/* The kernel AUTO has recorded for batches of `ntiles` tiles: 0 = not yet
- * measured, else SINGLE_STEP or MULTI_STEP; -1 for invalid arguments. */
+/* The kernel AUTO has recorded for batches of `ntiles` tiles at the default
+ * tile size (0: the batch's current members): 0 = not yet measured, else
+ * SINGLE_STEP or MULTI_STEP; -1 for invalid arguments.
+ * fhp_batch_get_tuned_tile_quads: the tile size recorded with it (0 = not
+ * yet measured). */
 FHP_API int fhp_batch_get_tuned_kernel(const fhp_batch* batch, int32_t ntiles);
+FHP_API int fhp_batch_get_tuned_tile_quads(const fhp_batch* batch, int32_t ntiles);
+/* Tile size of the batch kernels' work lists in quads (4 words, 128 nodes)
+ * per tile: 64, 128 or 256 (each tile whole rows of one member, at most 32
+ * KB of planes), or 0 = automatic (default: tuned online with the kernel,
+ * see above).  Results are identical for every size.
+ * fhp_batch_get_tile_quads returns the size of the current tile list. */
+FHP_API int fhp_batch_set_tile_quads(fhp_batch* batch, int32_t quads);
+FHP_API int fhp_batch_get_tile_quads(const fhp_batch* batch);
 /* Number of row tiles of the current members (the unit of the batch
  * kernels' work lists); -1 on error. */
 FHP_API int32_t fhp_batch_tile_count(fhp_batch* batch);
@@ -473,6 +489,33 @@ FHP_API int64_t fhp_batch_kernel_launches(const fhp_batch* batch);
 FHP_API int fhp_run_static(const uint8_t* device_bytes_in, uint8_t* device_bytes_out, int32_t width,
                            int32_t height, uint64_t seed, int64_t t0, int64_t n, double forcing_p,
                            void* stream);
+
+/* ------------------------------------------------------------------------
+ * Debug build (the library compiled with -DFHP_DEBUG: libfhp_gb300_debug.so).
+ * Its kernels check every index that addresses a lattice plane, a staged
+ * tile or a shared-memory ring against the buffer's extent before the
+ * access; a failing check skips the access and records the check's site in
+ * the kernel's error word, which fhp_synchronize / fhp_batch_synchronize
+ * report as FHP_EDEBUG.  Every region of a lattice's or batch member's
+ * device memory is followed by a 256-byte canary block.  No check traps.
+ * ------------------------------------------------------------------------ */
+
+/* 1 in the debug build, 0 in the release build. */
+FHP_API int fhp_debug_build(void);
+
+/* Compare the lattice's canary blocks with their fill (synchronous):
+ * *checked = blocks compared (0 in the release build, which has none),
+ * *corrupted = blocks whose bytes changed. */
+FHP_API int fhp_debug_canaries(fhp_lattice* lattice, int32_t* checked, int32_t* corrupted);
+
+/* As fhp_debug_canaries for every member of a batch. */
+FHP_API int fhp_batch_debug_canaries(fhp_batch* batch, int32_t* checked, int32_t* corrupted);
+
+/* Debug build: run one index check that fails on purpose and guards no
+ * access, and return the error word it left (kErrBounds bit 1 and its site
+ * code 99 in bits 8..15).  Shows that failing checks are recorded.
+ * FHP_EINVAL in the release build.  Synchronous; allocates one word. */
+FHP_API int fhp_debug_selftest(uint32_t* host_word);
 
 #ifdef __cplusplus
 }

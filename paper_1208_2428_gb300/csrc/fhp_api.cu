@@ -14,7 +14,10 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/fhp.h"
+#include "fhp_debug.cuh"
 #include "fhp_internal.h"
 
 struct fhp_lattice {
@@ -107,8 +110,17 @@ bool valid_size(int32_t W, int32_t H) {
     return W >= 32 && W % 32 == 0 && H >= 2 && H % 2 == 0 && (int64_t)W * H <= ((int64_t)1 << 40);
 }
 
+// Debug builds put a canary block of kCanaryBytes (filled with kCanaryByte)
+// after every region of a lattice's device memory; fhp_debug_canaries checks
+// them.  Release builds have none.
+constexpr size_t kCanaryBytes = fhp::kDebugBuild ? 256 : 0;
+constexpr unsigned char kCanaryByte = 0xA5;
+constexpr int kRegions = 6;
+
 struct Layout {
-    size_t plane_bytes, state_bytes, solid_off, flags_off, counters_off, staging_off, staging_bytes, total;
+    size_t plane_bytes, state_bytes, state1_off, solid_off, flags_off, counters_off, staging_off, staging_bytes,
+        total;
+    size_t canary_off[kRegions];   // one canary after each region (debug builds)
 };
 
 Layout layout(int32_t W, int32_t H) {
@@ -116,16 +128,23 @@ Layout layout(int32_t W, int32_t H) {
     Layout L;
     L.plane_bytes = round_up(g.plane_words * sizeof(uint32_t), 256);
     L.state_bytes = 7 * L.plane_bytes;
-    L.solid_off = 2 * L.state_bytes;
-    L.flags_off = L.solid_off + L.plane_bytes;
-    L.counters_off = L.flags_off + 256;  // one word per row covers any tiling
-    L.staging_off = L.counters_off + round_up((size_t)H * sizeof(unsigned int), 256);
+    L.canary_off[0] = L.state_bytes;
+    L.state1_off = L.state_bytes + kCanaryBytes;
+    L.canary_off[1] = L.state1_off + L.state_bytes;
+    L.solid_off = L.canary_off[1] + kCanaryBytes;
+    L.canary_off[2] = L.solid_off + L.plane_bytes;
+    L.flags_off = L.canary_off[2] + kCanaryBytes;
+    L.canary_off[3] = L.flags_off + 256;
+    L.counters_off = L.canary_off[3] + kCanaryBytes;  // one word per row covers any tiling
+    L.canary_off[4] = L.counters_off + round_up((size_t)H * sizeof(unsigned int), 256);
+    L.staging_off = L.canary_off[4] + kCanaryBytes;
     // W*H bytes, and at least the resident kernel's exchange rows for two
     // ghost rows per side (2 parities x 2 sides x 9 row planes of Pq words for
     // each of up to min(H/4, 256) strips).
     const size_t ghost_exchange = (size_t)144 * (H / 4 < 256 ? H / 4 : 256) * g.Pq;
     L.staging_bytes = round_up((size_t)W * H > ghost_exchange ? (size_t)W * H : ghost_exchange, 256);
-    L.total = L.staging_off + L.staging_bytes;
+    L.canary_off[5] = L.staging_off + L.staging_bytes;
+    L.total = L.canary_off[5] + kCanaryBytes;
     return L;
 }
 
@@ -210,6 +229,9 @@ int check_device_error(fhp_lattice* h) {
     if (word) {
         cudaMemsetAsync(h->flags + 1, 0, sizeof word, h->stream);
         cudaStreamSynchronize(h->stream);
+        if (word & fhp::kErrBounds)
+            return fail(h, FHP_EDEBUG, "a debug-build index check failed (site %u); the access was skipped",
+                        (word >> 8) & 0xFFu);
         return fail(h, FHP_ETIMEOUT, "a step kernel gave up waiting for its input copies; the state is unreliable");
     }
     return FHP_OK;
@@ -303,7 +325,7 @@ int fhp_create(fhp_lattice** out, const fhp_params* params) {
     }
     h->bytes = L.total;
     h->buf[0] = (uint32_t*)h->base;
-    h->buf[1] = (uint32_t*)(h->base + L.state_bytes);
+    h->buf[1] = (uint32_t*)(h->base + L.state1_off);
     h->solid = (uint32_t*)(h->base + L.solid_off);
     h->flags = (unsigned int*)(h->base + L.flags_off);
     h->tile_done = (unsigned int*)(h->base + L.counters_off);
@@ -311,6 +333,8 @@ int fhp_create(fhp_lattice** out, const fhp_params* params) {
     h->staging_bytes = L.staging_bytes;
     // Empty fluid lattice: zero both buffers and the solid plane.
     e = cudaMemsetAsync(h->base, 0, L.staging_off, h->stream);
+    for (int r = 0; r < kRegions && kCanaryBytes && e == cudaSuccess; ++r)
+        e = cudaMemsetAsync(h->base + L.canary_off[r], kCanaryByte, kCanaryBytes, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) {
         if (h->owns_memory) cudaFree(h->base);
@@ -434,7 +458,17 @@ int fhp_init_random(fhp_lattice* h, double density) {
     return FHP_OK;
 }
 
+namespace {
+// NVTX range for the duration of an API call (visible in Nsight tools; a
+// no-op without a tool attached).
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+};
+}  // namespace
+
 int fhp_step(fhp_lattice* h, int64_t n) {
+    NvtxRange nvtx("fhp_step");
     if (!h) return fail(nullptr, FHP_EINVAL, "lattice is NULL");
     if (n < 0) return fail(h, FHP_EINVAL, "negative step count %lld", (long long)n);
     if (n > kMaxTime - h->t) return fail(h, FHP_EINVAL, "step counter would pass 2^48");
@@ -538,6 +572,7 @@ int fhp_coarse_grain(fhp_lattice* h, int32_t block, int32_t* counts, float* rho,
 }
 
 int fhp_coarse_grain_device(fhp_lattice* h, int32_t block, int32_t* counts, float* rho, float* ux, float* uy) {
+    NvtxRange nvtx("fhp_coarse_grain");
     if (!h) return fail(nullptr, FHP_EINVAL, "lattice is NULL");
     int rc = check_block(h, block);
     if (rc != FHP_OK) return rc;
@@ -668,6 +703,7 @@ int fhp_get_temporal_block_kernel(const fhp_lattice* h) {
 }
 
 int fhp_autotune(fhp_lattice* h, int32_t trial_steps, int32_t* out_kernel, int32_t* out_temporal_block) {
+    NvtxRange nvtx("fhp_autotune");
     if (!h) return fail(nullptr, FHP_EINVAL, "lattice is NULL");
     if (trial_steps < 8 || trial_steps > 4096 || trial_steps % 8)
         return fail(h, FHP_EINVAL, "trial_steps %d must be a multiple of 8 in [8, 4096]", trial_steps);
@@ -778,6 +814,31 @@ int fhp_synchronize(fhp_lattice* h) {
 }
 
 int64_t fhp_kernel_launches(const fhp_lattice* h) { return h ? h->launches : -1; }
+
+int fhp_debug_build(void) { return fhp::kDebugBuild ? 1 : 0; }
+
+int fhp_debug_canaries(fhp_lattice* h, int32_t* checked, int32_t* corrupted) {
+    if (!h || !checked || !corrupted) return fail(h, FHP_EINVAL, "NULL argument");
+    *checked = 0;
+    *corrupted = 0;
+    if (!kCanaryBytes) return FHP_OK;
+    DeviceGuard dg(h->device);
+    const Layout L = layout(h->g.W, h->g.H);
+    std::vector<unsigned char> buf(kCanaryBytes);
+    for (int r = 0; r < kRegions; ++r) {
+        cudaError_t e = cudaMemcpyAsync(buf.data(), h->base + L.canary_off[r], kCanaryBytes, cudaMemcpyDeviceToHost,
+                                        h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess) return cuda_fail(h, e, "reading a canary");
+        ++*checked;
+        for (unsigned char c : buf)
+            if (c != kCanaryByte) {
+                ++*corrupted;
+                break;
+            }
+    }
+    return FHP_OK;
+}
 
 int fhp_philox4x32_10_device(const uint32_t* ctr, const uint32_t* key, uint32_t* out, int64_t n, void* stream) {
     if (!ctr || !key || !out || n < 0) return fail(nullptr, FHP_EINVAL, "invalid Philox arguments");

@@ -15,6 +15,7 @@
 // per-stage header in shared memory, and the consumers run the same per-quad
 // code against it.  Members whose budget is used up are skipped.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <cmath>
@@ -28,6 +29,7 @@
 
 #include "../../include/fhp.h"
 #include "fhp_arena.h"
+#include "fhp_debug.cuh"
 #include "fhp_device.cuh"
 #include "fhp_internal.h"
 #include "fhp_quad.cuh"
@@ -128,7 +130,8 @@ __device__ __forceinline__ void write_header(StageHeader* h, const DescCache& c,
         h->a.err = err;
         h->ta = c.ta;
         h->tile = tile;
-        h->active = s < c.steps;
+        h->active = s < c.steps && dbg_ok(tile >= 0 && tile < c.ta.ntiles, err, kSiteBatchTile) &&
+                    dbg_ok(8LL * c.ta.R * h->a.Pq * 4 <= kBStageBudget, err, kSiteStageFit);
         h->force = c.force;
     }
 }
@@ -457,8 +460,13 @@ struct Member {
 
 constexpr int64_t kMaxTime = (int64_t)1 << 48;
 
+// Debug builds follow every member block with a canary of kCanaryBytes
+// (filled with kCanaryByte), checked by fhp_batch_debug_canaries.
+constexpr size_t kCanaryBytes = fhp::kDebugBuild ? 256 : 0;
+constexpr unsigned char kCanaryByte = 0xA5;
+
 size_t member_bytes(const fhp::Geometry& g) {
-    return 15 * fhp::round256(g.plane_words * sizeof(uint32_t)) + 256;
+    return 15 * fhp::round256(g.plane_words * sizeof(uint32_t)) + 256 + kCanaryBytes;
 }
 
 struct DeviceGuard {
@@ -475,12 +483,17 @@ struct DeviceGuard {
 }  // namespace
 
 constexpr int kTuneClasses = 32;
-constexpr int kTuneMinSteps = 16;   // a trial runs at least this many steps with each kernel
+constexpr int kTuneMinSteps = 16;   // a trial runs at least this many steps with each candidate
+constexpr int kTuneCands = 4;       // (kernel, tile quads) pairs a trial compares
+constexpr int kDefaultTileQuads = 256;
 
 struct TuneTrial {
     int cls = -1;                    // class being measured, -1: none in flight
-    cudaEvent_t ev[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // [single, multi][start, end]
-    double updates[2] = {0.0, 0.0};
+    int ncand = 0;
+    int kind[kTuneCands] = {};
+    int quads[kTuneCands] = {};
+    cudaEvent_t ev[kTuneCands][2] = {};   // [candidate][start, end]
+    double updates[kTuneCands] = {};
 };
 
 struct fhp_batch {
@@ -499,6 +512,9 @@ struct fhp_batch {
     unsigned int* d_done = nullptr;             // per-tile counters of the multi-step kernel
     int step_kernel = FHP_BATCH_KERNEL_AUTO;
     int tuned[kTuneClasses] = {};               // per tile-count class: kernel measured fastest (0: unknown)
+    int tuned_quads[kTuneClasses] = {};         // ... and its tile size (quads per tile)
+    int tile_quads = 0;                         // quads per tile: 0 automatic (tuned with the kernel)
+    int cur_quads = kDefaultTileQuads;          // tile size of the current tile list
     TuneTrial trial;
     int* d_step_base = nullptr;
     unsigned int* d_err = nullptr;
@@ -571,11 +587,11 @@ int ensure_tables(fhp_batch* b, size_t lats, size_t tiles) {
     return FHP_OK;
 }
 
-// Rows per tile: about one quad per consumer thread (256 per tile), and the
-// tile's 8 planes within one stage.
-int rows_per_tile(const fhp::Geometry& g) {
+// Rows per tile: about `quads` quads per tile (256: one per consumer
+// thread), and the tile's 8 planes within one stage.
+int rows_per_tile(const fhp::Geometry& g, int quads = kDefaultTileQuads) {
     const long long row_bytes = 8LL * g.Pq * 4;
-    int R = (fhp::kBConsumerWarps * 32 + g.nq - 1) / g.nq;
+    int R = (quads + g.nq - 1) / g.nq;
     const int fit = (int)(fhp::kBStageBudget / row_bytes);
     R = std::min(R, fit);
     R = std::min(R, g.H);
@@ -682,8 +698,10 @@ int fhp_batch_add(fhp_batch* b, int32_t width, int32_t height, uint64_t seed, do
     m.buf[1] = (uint32_t*)(base + 7 * pb);
     m.solid = (uint32_t*)(base + 14 * pb);
     m.flags = (unsigned int*)(base + 15 * pb);
-    m.R = rows_per_tile(g);
-    cudaError_t e = cudaMemsetAsync(base, 0, m.bytes, b->stream);
+    m.R = rows_per_tile(g, b->cur_quads);
+    cudaError_t e = cudaMemsetAsync(base, 0, m.bytes - kCanaryBytes, b->stream);
+    if (e == cudaSuccess && kCanaryBytes)
+        e = cudaMemsetAsync(base + m.bytes - kCanaryBytes, kCanaryByte, kCanaryBytes, b->stream);
     if (e != cudaSuccess) {
         b->arena.release(m.off, m.bytes);
         return bcuda(b, e, "clearing a new member");
@@ -950,6 +968,29 @@ int prepare_tiles(fhp_batch* b) {
     return ensure_tables(b, std::max<size_t>(nm, 1), std::max<size_t>(b->h_tiles.size(), 1));
 }
 
+// Tiles of the members at a tile size of `quads` (the tuning classes are
+// keyed by the count at the default size, so that a class does not change
+// with the size tried).
+int tiles_at(const fhp_batch* b, int quads) {
+    long long n = 0;
+    for (const Member& m : b->members)
+        if (m.used) {
+            const int R = rows_per_tile(m.g, quads);
+            n += (m.g.H + R - 1) / R;
+        }
+    return (int)std::min<long long>(n, 1 << 30);
+}
+
+// Re-tile every member at `quads` quads per tile (results do not depend on
+// the tiling).
+void apply_tile_quads(fhp_batch* b, int quads) {
+    if (quads == b->cur_quads) return;
+    b->cur_quads = quads;
+    for (Member& m : b->members)
+        if (m.used) m.R = rows_per_tile(m.g, quads);
+    b->tiles_dirty = true;
+}
+
 // Uploads the descriptors of a call of `chunk` steps (each member advances
 // min(chunk, its budget) steps); returns the largest count in *max_steps.
 int upload_descriptors(fhp_batch* b, int chunk, std::vector<int>& steps_of, int* max_steps) {
@@ -1124,17 +1165,21 @@ int tile_class(int ntiles) {
 void collect_trial(fhp_batch* b) {
     TuneTrial& tr = b->trial;
     if (tr.cls < 0) return;
-    for (int k = 0; k < 2; ++k)
+    for (int k = 0; k < tr.ncand; ++k)
         if (cudaEventQuery(tr.ev[k][1]) != cudaSuccess) return;  // not finished yet: look again next call
-    float ms[2] = {0.0f, 0.0f};
-    bool ok = true;
-    for (int k = 0; k < 2; ++k) ok = ok && cudaEventElapsedTime(&ms[k], tr.ev[k][0], tr.ev[k][1]) == cudaSuccess;
-    if (ok && ms[0] > 0.0f && ms[1] > 0.0f) {
-        const double rate_single = tr.updates[0] / ms[0], rate_multi = tr.updates[1] / ms[1];
-        b->tuned[tr.cls] = rate_multi > rate_single ? FHP_BATCH_KERNEL_MULTI_STEP : FHP_BATCH_KERNEL_SINGLE_STEP;
-    } else {
-        b->tuned[tr.cls] = FHP_BATCH_KERNEL_SINGLE_STEP;
+    int best = -1;
+    double best_rate = 0.0;
+    for (int k = 0; k < tr.ncand; ++k) {
+        float ms = 0.0f;
+        if (cudaEventElapsedTime(&ms, tr.ev[k][0], tr.ev[k][1]) != cudaSuccess || !(ms > 0.0f)) continue;
+        const double rate = tr.updates[k] / ms;
+        if (best < 0 || rate > best_rate) {
+            best = k;
+            best_rate = rate;
+        }
     }
+    b->tuned[tr.cls] = best >= 0 ? tr.kind[best] : FHP_BATCH_KERNEL_SINGLE_STEP;
+    b->tuned_quads[tr.cls] = best >= 0 ? tr.quads[best] : kDefaultTileQuads;
     tr.cls = -1;
 }
 
@@ -1163,7 +1208,19 @@ int run_chunk(fhp_batch* b, int chunk, int kind, std::vector<int>& steps_of, dou
 
 }  // namespace
 
+namespace {
+int batch_step(fhp_batch* b, int64_t n);
+}  // namespace
+
 int fhp_batch_step(fhp_batch* b, int64_t n) {
+    nvtxRangePushA("fhp_batch_step");
+    const int rc = batch_step(b, n);
+    nvtxRangePop();
+    return rc;
+}
+
+namespace {
+int batch_step(fhp_batch* b, int64_t n) {
     if (!b || n < 0) return bfail(b, FHP_EINVAL, "invalid arguments");
     DeviceGuard dg(b->device);
     for (auto& m : b->members) {
@@ -1176,30 +1233,52 @@ int fhp_batch_step(fhp_batch* b, int64_t n) {
     if (rc != FHP_OK) return rc;
     std::vector<int> steps_of;
     int64_t left = n;
+    const int cls = tile_class(tiles_at(b, kDefaultTileQuads));
     if (b->step_kernel == FHP_BATCH_KERNEL_AUTO && b->ntiles > 0) {
         collect_trial(b);
-        const int cls = tile_class(b->ntiles);
-        // A trial needs halves long enough for the single-step kernel to run
-        // as it normally does (from the captured graph).
-        const int64_t min_half = std::max<int64_t>(kTuneMinSteps, b->graph_steps);
-        if (b->tuned[cls] == FHP_BATCH_KERNEL_AUTO && b->trial.cls < 0 && n >= 2 * min_half) {
-            // A trial: half of the call with each kernel.
+        // Candidates: both kernels, and with an automatic tile size two
+        // sizes (256 and 128 quads per tile).  A trial needs parts long
+        // enough for the single-step kernel to run as it normally does (from
+        // the captured graph).
+        TuneTrial& tr = b->trial;
+        int nc = 0;
+        const int sizes[2] = {kDefaultTileQuads, kDefaultTileQuads / 2};
+        for (int si = 0; si < (b->tile_quads ? 1 : 2); ++si)
+            for (int kind : {FHP_BATCH_KERNEL_SINGLE_STEP, FHP_BATCH_KERNEL_MULTI_STEP}) {
+                tr.kind[nc] = kind;
+                tr.quads[nc] = b->tile_quads ? b->tile_quads : sizes[si];
+                ++nc;
+            }
+        const int64_t min_part = std::max<int64_t>(kTuneMinSteps, b->graph_steps);
+        if (b->tuned[cls] == FHP_BATCH_KERNEL_AUTO && tr.cls < 0 && n >= nc * min_part) {
+            // A trial: an equal part of the call with each candidate.
             rc = ensure_trial_events(b);
             if (rc != FHP_OK) return rc;
-            const int half = (int)std::min<int64_t>(n / 2, (int64_t)1 << 20);
-            const int kinds[2] = {FHP_BATCH_KERNEL_SINGLE_STEP, FHP_BATCH_KERNEL_MULTI_STEP};
-            for (int k = 0; k < 2; ++k) {
-                cudaEventRecord(b->trial.ev[k][0], b->stream);
-                b->trial.updates[k] = 0.0;
-                rc = run_chunk(b, half, kinds[k], steps_of, &b->trial.updates[k]);
+            const int part = (int)std::min<int64_t>(n / nc, (int64_t)1 << 20);
+            tr.ncand = nc;
+            for (int k = 0; k < nc; ++k) {
+                apply_tile_quads(b, tr.quads[k]);
+                rc = prepare_tiles(b);
                 if (rc != FHP_OK) return rc;
-                cudaError_t e = cudaEventRecord(b->trial.ev[k][1], b->stream);
+                cudaEventRecord(tr.ev[k][0], b->stream);
+                tr.updates[k] = 0.0;
+                rc = run_chunk(b, part, tr.kind[k], steps_of, &tr.updates[k]);
+                if (rc != FHP_OK) return rc;
+                cudaError_t e = cudaEventRecord(tr.ev[k][1], b->stream);
                 if (e != cudaSuccess) return bcuda(b, e, "recording the tuning events");
             }
-            b->trial.cls = cls;
-            left -= 2 * half;
+            tr.cls = cls;
+            left -= (int64_t)nc * part;
         }
     }
+    // The tile size for the rest of the call: the caller's, else the one
+    // recorded for the class, else the default.
+    int quads = b->tile_quads;
+    if (!quads) quads = (b->step_kernel == FHP_BATCH_KERNEL_AUTO && b->tuned_quads[cls]) ? b->tuned_quads[cls]
+                                                                                             : kDefaultTileQuads;
+    apply_tile_quads(b, quads);
+    rc = prepare_tiles(b);
+    if (rc != FHP_OK) return rc;
     while (left > 0) {
         // Calls are split into chunks of at most 2^24 steps: the multi-step
         // kernel's counters grow by kBConsumerWarps per tile and step.
@@ -1208,7 +1287,7 @@ int fhp_batch_step(fhp_batch* b, int64_t n) {
         const int chunk = (int)std::min<int64_t>(left, (int64_t)1 << 24);
         int kind = b->step_kernel;
         if (kind == FHP_BATCH_KERNEL_AUTO) {
-            const int t = b->tuned[tile_class(b->ntiles)];
+            const int t = b->tuned[cls];
             kind = t == FHP_BATCH_KERNEL_AUTO ? FHP_BATCH_KERNEL_SINGLE_STEP : t;
         }
         rc = run_chunk(b, chunk, kind, steps_of, nullptr);
@@ -1218,15 +1297,54 @@ int fhp_batch_step(fhp_batch* b, int64_t n) {
     return FHP_OK;
 }
 
+}  // namespace
+
 int fhp_batch_get_tuned_kernel(const fhp_batch* b, int32_t ntiles) {
-    if (!b || ntiles < 1) return -1;
-    return b->tuned[tile_class(ntiles)];
+    if (!b || ntiles < 0) return -1;
+    return b->tuned[tile_class(ntiles ? ntiles : tiles_at(b, kDefaultTileQuads))];
 }
+
+int fhp_batch_get_tuned_tile_quads(const fhp_batch* b, int32_t ntiles) {
+    if (!b || ntiles < 0) return -1;
+    return b->tuned_quads[tile_class(ntiles ? ntiles : tiles_at(b, kDefaultTileQuads))];
+}
+
+int fhp_batch_set_tile_quads(fhp_batch* b, int32_t quads) {
+    if (!b || (quads != 0 && quads != 64 && quads != 128 && quads != 256))
+        return bfail(b, FHP_EINVAL, "tile size %d not in {0, 64, 128, 256}", quads);
+    b->tile_quads = quads;
+    return FHP_OK;
+}
+
+int fhp_batch_get_tile_quads(const fhp_batch* b) { return b ? b->cur_quads : -1; }
 
 int32_t fhp_batch_tile_count(fhp_batch* b) {
     if (!b) return -1;
     if (prepare_tiles(b) != FHP_OK) return -1;
     return b->ntiles;
+}
+
+int fhp_batch_debug_canaries(fhp_batch* b, int32_t* checked, int32_t* corrupted) {
+    if (!b || !checked || !corrupted) return bfail(b, FHP_EINVAL, "NULL argument");
+    *checked = 0;
+    *corrupted = 0;
+    if (!kCanaryBytes) return FHP_OK;
+    DeviceGuard dg(b->device);
+    std::vector<unsigned char> buf(kCanaryBytes);
+    for (const Member& m : b->members) {
+        if (!m.used) continue;
+        cudaError_t e = cudaMemcpyAsync(buf.data(), b->arena_base + m.off + m.bytes - kCanaryBytes, kCanaryBytes,
+                                        cudaMemcpyDeviceToHost, b->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+        if (e != cudaSuccess) return bcuda(b, e, "reading a canary");
+        ++*checked;
+        for (unsigned char c : buf)
+            if (c != kCanaryByte) {
+                ++*corrupted;
+                break;
+            }
+    }
+    return FHP_OK;
 }
 
 int fhp_batch_set_step_kernel(fhp_batch* b, int32_t kind) {
@@ -1248,6 +1366,9 @@ int fhp_batch_synchronize(fhp_batch* b) {
     if (e != cudaSuccess) return bcuda(b, e, "reading the error word");
     if (word) {
         cudaMemset(b->d_err, 0, sizeof word);
+        if (word & fhp::kErrBounds)
+            return bfail(b, FHP_EDEBUG, "a debug-build index check failed (site %u); the access was skipped",
+                         (word >> 8) & 0xFFu);
         return bfail(b, FHP_ETIMEOUT, "a batch kernel gave up waiting for its input copies");
     }
     return FHP_OK;

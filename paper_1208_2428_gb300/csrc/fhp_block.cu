@@ -16,6 +16,7 @@
 #include <cstdio>
 #include <mutex>
 
+#include "fhp_debug.cuh"
 #include "fhp_device.cuh"
 #include "fhp_internal.h"
 #include "fhp_quad.cuh"
@@ -81,6 +82,7 @@ __device__ void stage_tile(const StepArgs& a, const BlockArgs& b, int tile, uint
         for (int job = rl; job < NP * rows; job += lanes) {
             const int slot = job / rows, r = job - slot * rows;
             const int y = wrap(y0 - b.k + r, a.H);
+            if (!dbg_ok(r < kRin && col < kQI && q >= 0 && q < a.nq, a.err, kSiteBlockStage)) continue;
             const uint32_t* plane = slot < 7 ? a.src + (size_t)slot * a.plane_words : a.solid;
             uint32_t* srow = (slot < 7 ? A + slot * pws : S) + (size_t)r * kRowWords;
             cp_async16(srow + 4 * col, plane + (size_t)y * a.Pq + 4 * q);
@@ -123,6 +125,7 @@ __device__ __forceinline__ void block_step(const StepArgs& a, const BlockArgs& b
         const int r = it < n_even ? first_even + 2 * it : first_odd + 2 * (it - n_even);
         const int y = wrap(y0 - b.k + r, a.H);
         const int w = 4 * c;
+        if (!dbg_ok(r >= 1 && r + 1 < kRin && c < kQI, a.err, kSiteBlockStage)) continue;
         const uint32_t* rowm = src + (size_t)(r - 1) * kRowWords;
         const uint32_t* row0 = src + (size_t)r * kRowWords;
         const uint32_t* rowp = src + (size_t)(r + 1) * kRowWords;

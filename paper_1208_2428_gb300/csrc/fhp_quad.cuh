@@ -6,6 +6,7 @@
 // and the completion counters of the multi-step kernels.
 #pragma once
 
+#include "fhp_debug.cuh"
 #include "fhp_device.cuh"
 #include "fhp_internal.h"
 
@@ -107,6 +108,7 @@ __device__ __forceinline__ void store_quad(const StepArgs& a, uint32_t* dst, int
             o[k].w = 0u;
         }
     }
+    if (!dbg_ok(y >= 0 && y < a.H && q >= 0 && q < a.nq, a.err, kSiteStoreQuad)) return;
     const size_t pw = a.plane_words;
     uint32_t* d = dst + (size_t)y * a.Pq + 4 * q;
 #pragma unroll
@@ -196,6 +198,7 @@ __device__ void issue_tile(const StepArgs& a, const TileArgs& ta, const uint32_t
             if (yy < 0) yy += a.H;
             if (yy >= a.H) yy -= a.H;
             const int run = min(rows - r, a.H - yy);  // contiguous rows up to the end of the plane
+            if (!dbg_ok(yy >= 0 && yy < a.H && run >= 1 && r + run <= ta.R, a.err, kSiteIssueTile)) break;
             bulk_copy_g2s(stage + ((size_t)slot * ta.R + r) * a.Pq, plane + (size_t)yy * a.Pq,
                           (uint32_t)run * row_bytes, bar);
             r += run;
@@ -211,6 +214,9 @@ __device__ __forceinline__ void quad_from_stage(const StepArgs& a, const StepVar
     const int m = RAGGED ? (q == a.nq - 1 ? a.Wq - w : 4) : 4;
     const int wl = q == 0 ? a.Wq - 1 : w - 1;       // word left of the quad (periodic)
     const int wr = q == a.nq - 1 ? 0 : w + 4;       // word right of the quad (periodic)
+    if (!dbg_ok(r >= 0 && r < R && q >= 0 && q < a.nq && w + 3 < Pq && wl >= 0 && wl < a.Wq && wr < a.Wq, a.err,
+                kSiteStageQuad))
+        return;
     const uint32_t* s0 = stage + (size_t)r * Pq;    // slot 0, row r
     const size_t slot = (size_t)R * Pq;
     const uint4 i0 = ld4(s0 + 0 * slot + w), i1 = ld4(s0 + 1 * slot + w);

@@ -58,6 +58,7 @@ __global__ void __launch_bounds__(kTmaThreads, SAT ? 1 : 2) fhp_step_tma_kernel(
     uint32_t* stages = reinterpret_cast<uint32_t*>(smem_raw + kBarrierBytes);
     constexpr int NP = SOLID ? 8 : 7;
     const size_t stage_words = (size_t)NP * ta.R * a.Pq;
+    if (!dbg_ok(stage_words * 4 <= (size_t)kStageBudget, a.err, kSiteStageFit)) return;
     // Tiles of this CTA: blockIdx.x, blockIdx.x + gridDim.x, ...
     const int count = (ta.ntiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
     auto tile_of = [&](int i) { return (int)blockIdx.x + i * (int)gridDim.x; };
@@ -141,6 +142,7 @@ __global__ void __launch_bounds__(kRunThreads, SAT ? 1 : 2) fhp_run_kernel(const
     uint32_t* stages = reinterpret_cast<uint32_t*>(smem_raw + kBarrierBytes);
     constexpr int NP = SOLID ? 8 : 7;
     const size_t stage_words = (size_t)NP * ta.R * a.Pq;
+    if (!dbg_ok(stage_words * 4 <= (size_t)kStageBudget, a.err, kSiteStageFit)) return;
     const int count = (ta.ntiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
@@ -320,16 +322,20 @@ __device__ __forceinline__ uint32_t right_word(uint4 v, uint32_t fallback, const
 template <bool SOLID, bool FORCE, bool RAGGED, bool ODD, bool SAT>
 __device__ __forceinline__ void direct_quad(const StepArgs& a, const Lane& L) {
     const size_t pw = a.plane_words;
-    const int y = L.y;
+    // Debug builds: an index outside the lattice reads row 0 / quad 0 instead
+    // and stores nothing (the lanes must still take part in the shuffles).
+    const bool in_range = dbg_ok(L.y >= 0 && L.y < a.H && L.q >= 0 && L.q < a.nq, a.err, kSiteDirectQuad);
+    const int y = in_range ? L.y : 0;
     const int ym = y == 0 ? a.H - 1 : y - 1;
     const int yp = y == a.H - 1 ? 0 : y + 1;
-    const int w = 4 * L.q;
+    const int qi = in_range ? L.q : 0;
+    const int w = 4 * qi;
     const uint32_t* rm = a.src + (size_t)ym * a.Pq;  // row y-1 of plane 0
     const uint32_t* r0 = a.src + (size_t)y * a.Pq;   // row y
     const uint32_t* rp = a.src + (size_t)yp * a.Pq;  // row y+1
-    const int m = RAGGED ? (L.q == a.nq - 1 ? a.Wq - w : 4) : 4;
-    const int wl = L.q == 0 ? a.Wq - 1 : w - 1;
-    const int wr = L.q == a.nq - 1 ? 0 : w + 4;
+    const int m = RAGGED ? (qi == a.nq - 1 ? a.Wq - w : 4) : 4;
+    const int wl = qi == 0 ? a.Wq - 1 : w - 1;
+    const int wr = qi == a.nq - 1 ? 0 : w + 4;
 
     const uint4 i3 = ld4(rm + 3 * pw + w), i4 = ld4(rm + 4 * pw + w);
     const uint4 i2 = ld4(r0 + 2 * pw + w), i5 = ld4(r0 + 5 * pw + w);
@@ -361,7 +367,7 @@ __device__ __forceinline__ void direct_quad(const StepArgs& a, const Lane& L) {
         n1 = i1;
     }
     const StepVar v{a.dst, a.t_lo, a.t_hi};
-    finish_quad<SOLID, FORCE, RAGGED, SAT>(a, v, L.q, y, m, n0, n1, n2, n3, n4, n5, i6, sd, L.active);
+    finish_quad<SOLID, FORCE, RAGGED, SAT>(a, v, L.q, y, m, n0, n1, n2, n3, n4, n5, i6, sd, L.active && in_range);
 }
 
 // SAT: the FHP-III rule set (its larger scattering network gets twice the

@@ -35,6 +35,7 @@
 #include <cstdio>
 #include <mutex>
 
+#include "fhp_debug.cuh"
 #include "fhp_device.cuh"
 #include "fhp_internal.h"
 #include "fhp_quad.cuh"
@@ -192,6 +193,15 @@ __global__ void __launch_bounds__(kWaveThreads, 1) fhp_wave_kernel(const StepArg
     unsigned int* wr = rd + (K + 1) * C * P;                                            // [K+1][C][P]
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     __shared__ int abort_flag;
+    {
+        unsigned int dyn;
+        asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dyn));
+        const size_t need = (size_t)kWaveHeaderBytes +
+                            ((size_t)wa.D0 * slot0_words + (size_t)(K - 1) * wa.D * slot_words) * 4;
+        if (!dbg_ok(need <= dyn && wa.D0 <= kWaveMaxD0 && (K + 1) * C * P * 8 <= kWaveCounterBytes, a.err,
+                    kSiteWaveSmem))
+            return;
+    }
 
     if (threadIdx.x == 0) abort_flag = 0;
     for (int band = blockIdx.x; band < wa.nbands; band += gridDim.x) {
@@ -263,7 +273,7 @@ __global__ void __launch_bounds__(kWaveThreads, 1) fhp_wave_kernel(const StepArg
             const int rem = warp - (j - 1) * C * P;
             const int c = rem / P, p = rem - c * P;
             const int q = c * 32 + lane;
-            const bool active = q < a.nq;
+            const bool active = q < a.nq && dbg_ok(4 * q + 3 < Pq && a.Wq <= Pq, a.err, kSiteWaveQuad);
             const int nj = B + 2 * (K - j);
             const int start = y0 - (K - j);
             const unsigned long long t = wa.t0 + (unsigned long long)(j - 1);

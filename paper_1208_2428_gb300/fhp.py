@@ -16,10 +16,14 @@ import numpy as np
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "_lib", "libfhp_gb300.so")
+# The debug build (device-side index checks, canary blocks; see fhp.h) is
+# loaded instead when the environment sets FHP_DEBUG=1.
+DEBUG_LIB_PATH = os.path.join(_PKG, "_lib", "libfhp_gb300_debug.so")
 HEADER = os.path.join(os.path.dirname(_PKG), "include", "fhp.h")
 
-FHP_OK, FHP_EINVAL, FHP_ENOMEM, FHP_ECUDA, FHP_ETIMEOUT, FHP_EBUSY = range(6)
-_ERRNAMES = {1: "FHP_EINVAL", 2: "FHP_ENOMEM", 3: "FHP_ECUDA", 4: "FHP_ETIMEOUT", 5: "FHP_EBUSY"}
+FHP_OK, FHP_EINVAL, FHP_ENOMEM, FHP_ECUDA, FHP_ETIMEOUT, FHP_EBUSY, FHP_EDEBUG = range(7)
+_ERRNAMES = {1: "FHP_EINVAL", 2: "FHP_ENOMEM", 3: "FHP_ECUDA", 4: "FHP_ETIMEOUT", 5: "FHP_EBUSY",
+             6: "FHP_EDEBUG"}
 
 _lib = None
 
@@ -60,11 +64,12 @@ def exported_names() -> list[str]:
 
 
 def load(path: str | None = None):
-    """Load libfhp_gb300.so (raises if it has not been built)."""
+    """Load libfhp_gb300.so, or its debug build when FHP_DEBUG=1 is set
+    (raises if the library has not been built)."""
     global _lib
     if _lib is not None:
         return _lib
-    p = path or LIB_PATH
+    p = path or (DEBUG_LIB_PATH if os.environ.get("FHP_DEBUG") == "1" else LIB_PATH)
     if not os.path.exists(p):
         raise ImportError(f"{p} is missing: build the CUDA library first "
                           "(python -c 'import __graft_entry__ as g; g.build()')")
@@ -113,6 +118,9 @@ def load(path: str | None = None):
         "fhp_batch_coarse_grain_device": (ctypes.c_int, [vp, i32, i32, vp, vp, vp, vp, vp]),
         "fhp_batch_get_step_kernel": (ctypes.c_int, [vp]),
         "fhp_batch_get_tuned_kernel": (ctypes.c_int, [vp, i32]),
+        "fhp_batch_get_tuned_tile_quads": (ctypes.c_int, [vp, i32]),
+        "fhp_batch_set_tile_quads": (ctypes.c_int, [vp, i32]),
+        "fhp_batch_get_tile_quads": (ctypes.c_int, [vp]),
         "fhp_batch_tile_count": (i32, [vp]),
         "fhp_batch_load_obstacles": (ctypes.c_int, [vp, i32, u8p]),
         "fhp_batch_lattice_bytes": (ctypes.c_size_t, [i32, i32]),
@@ -135,6 +143,11 @@ def load(path: str | None = None):
         "fhp_batch_count": (i32, [vp]),
         "fhp_batch_free_bytes": (ctypes.c_size_t, [vp]),
         "fhp_batch_kernel_launches": (i64, [vp]),
+        "fhp_debug_build": (ctypes.c_int, []),
+        "fhp_debug_canaries": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
+        "fhp_batch_debug_canaries": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_int32),
+                                                    ctypes.POINTER(ctypes.c_int32)]),
+        "fhp_debug_selftest": (ctypes.c_int, [ctypes.POINTER(ctypes.c_uint32)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -346,6 +359,12 @@ class Lattice:
     def synchronize(self):
         self._check(self._lib.fhp_synchronize(self._h))
 
+    def debug_canaries(self) -> tuple[int, int]:
+        """(canary blocks checked, blocks corrupted); (0, 0) in the release build."""
+        checked, corrupted = ctypes.c_int32(0), ctypes.c_int32(0)
+        self._check(self._lib.fhp_debug_canaries(self._h, ctypes.byref(checked), ctypes.byref(corrupted)))
+        return checked.value, corrupted.value
+
     @property
     def kernel_launches(self) -> int:
         return int(self._lib.fhp_kernel_launches(self._h))
@@ -540,9 +559,24 @@ class Batch:
         return int(self._lib.fhp_batch_tile_count(self._h))
 
     def tuned_kernel(self, ntiles: int | None = None) -> int:
-        """Kernel the automatic choice recorded for this many tiles (0: none yet)."""
-        n = self.tile_count if ntiles is None else int(ntiles)
+        """Kernel the automatic choice recorded for this many tiles at the
+        default tile size (None: the current members; 0: none yet)."""
+        n = 0 if ntiles is None else int(ntiles)
         return int(self._lib.fhp_batch_get_tuned_kernel(self._h, n))
+
+    def tuned_tile_quads(self, ntiles: int | None = None) -> int:
+        """Tile size recorded with the tuned kernel (0: none yet)."""
+        n = 0 if ntiles is None else int(ntiles)
+        return int(self._lib.fhp_batch_get_tuned_tile_quads(self._h, n))
+
+    def set_tile_quads(self, quads: int):
+        """Quads (128-node units) per tile: 64, 128, 256, or 0 = tuned online."""
+        self._check(self._lib.fhp_batch_set_tile_quads(self._h, int(quads)))
+
+    @property
+    def tile_quads(self) -> int:
+        """Tile size of the current tile list."""
+        return int(self._lib.fhp_batch_get_tile_quads(self._h))
 
     def set_graph_steps(self, n: int):
         self._check(self._lib.fhp_batch_set_graph_steps(self._h, int(n)))
@@ -560,6 +594,12 @@ class Batch:
 
     def synchronize(self):
         self._check(self._lib.fhp_batch_synchronize(self._h))
+
+    def debug_canaries(self) -> tuple[int, int]:
+        """(canary blocks checked, blocks corrupted) over the members; (0, 0) in the release build."""
+        checked, corrupted = ctypes.c_int32(0), ctypes.c_int32(0)
+        self._check(self._lib.fhp_batch_debug_canaries(self._h, ctypes.byref(checked), ctypes.byref(corrupted)))
+        return checked.value, corrupted.value
 
     @property
     def count(self) -> int:

@@ -53,3 +53,17 @@ def test_required_bytes_and_validation_without_gpu(lib):
     assert lib.fhp_create(ctypes.byref(out), ctypes.byref(p)) == fhp.FHP_EINVAL
     assert lib.fhp_step(None, 1) == fhp.FHP_EINVAL
     lib.fhp_destroy(None)
+
+
+def test_debug_build_exports_every_declared_symbol():
+    path = cuda_build.build(debug=True)
+    dbg = ctypes.CDLL(path)
+    missing = [n for n in fhp.exported_names() if not hasattr(dbg, n)]
+    assert not missing, missing
+    dbg.fhp_debug_build.restype = ctypes.c_int
+    assert dbg.fhp_debug_build() == 1
+    # the debug layout adds six 256-byte canary blocks to a lattice's bytes
+    dbg.fhp_required_bytes.restype = ctypes.c_size_t
+    dbg.fhp_required_bytes.argtypes = [ctypes.c_int32, ctypes.c_int32]
+    rel = fhp.load()
+    assert dbg.fhp_required_bytes(256, 64) == rel.fhp_required_bytes(256, 64) + 6 * 256

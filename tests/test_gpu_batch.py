@@ -183,9 +183,10 @@ def test_multi_step_kernel_edge_cases(pkg, oracle_mod):
 
 
 def test_automatic_choice_is_tuned_online_and_exact(pkg, oracle_mod):
-    """The automatic kernel choice times both kernels on a first long call
-    (half of its steps each) and records the faster for the batch's size
-    class; members stay bit-exact throughout."""
+    """The automatic choice times both kernels at two tile sizes (256 and 128
+    quads per tile) on a first long call (a quarter of its steps each) and
+    records the fastest pair for the batch's size class; members stay
+    bit-exact throughout, across the re-tiling."""
     jobs = small_ensemble(10, 5)
     states = [j.initial_state() for j in jobs]
     arena = sum(pkg.Batch.lattice_bytes(j.W, j.H) for j in jobs) + (64 << 20)
@@ -196,22 +197,52 @@ def test_automatic_choice_is_tuned_online_and_exact(pkg, oracle_mod):
             k = b.add(j.W, j.H, j.seed, j.p)
             b.set_state(k, s0)
             slots.append(k)
-        assert b.tuned_kernel() == 0
+        assert b.tuned_kernel() == 0 and b.tuned_tile_quads() == 0 and b.tile_quads == 256
         b.set_graph_steps(8)
-        b.step(14)                 # too short for a trial (halves below 16 steps)
+        b.step(14)                 # too short for a trial (four parts of at least 16 steps)
         b.synchronize()
         b.step(1)
         assert b.tuned_kernel() == 0
-        b.step(40)                 # a trial: 20 steps with each kernel
+        b.step(64)                 # a trial: 16 steps with each (kernel, tile size)
         b.synchronize()
         b.step(3)                  # reads the trial's events
         assert b.tuned_kernel() in (1, 2)
+        assert b.tuned_tile_quads() in (128, 256)
+        assert b.tile_quads == b.tuned_tile_quads()
         b.step(6)
         b.synchronize()
         for j, s0, k in zip(jobs, states, slots):
-            want, _ = oracle_mod.run(s0, j.seed, 0, 64, j.p)
-            assert b.time(k) == 64
+            want, _ = oracle_mod.run(s0, j.seed, 0, 88, j.p)
+            assert b.time(k) == 88
             assert np.array_equal(b.get_state(k), want), j.name
+
+
+@pytest.mark.parametrize("kernel", [1, 2])
+def test_tile_sizes_are_exact(pkg, oracle_mod, kernel):
+    """Every tile size (64, 128, 256 quads per tile), changed between calls,
+    gives each member its oracle run bit for bit with either batch kernel."""
+    jobs = small_ensemble(6, 11)
+    states = [j.initial_state() for j in jobs]
+    arena = sum(pkg.Batch.lattice_bytes(j.W, j.H) for j in jobs) + (64 << 20)
+    with pkg.Batch(arena) as b:
+        b.set_step_kernel(kernel)
+        slots = []
+        for j, s0 in zip(jobs, states):
+            k = b.add(j.W, j.H, j.seed, j.p)
+            b.set_state(k, s0)
+            slots.append(k)
+        n = 0
+        for quads, steps in ((64, 5), (256, 4), (128, 6), (64, 3)):
+            b.set_tile_quads(quads)
+            b.step(steps)
+            n += steps
+            assert b.tile_quads == quads
+        b.synchronize()
+        for j, s0, k in zip(jobs, states, slots):
+            want, _ = oracle_mod.run(s0, j.seed, 0, n, j.p)
+            assert np.array_equal(b.get_state(k), want), (j.name, kernel)
+        with pytest.raises(pkg.FhpError):
+            b.set_tile_quads(96)
 
 
 def test_ensemble_512_in_the_benchmark_configuration(pkg, oracle_mod):
@@ -237,9 +268,9 @@ def test_ensemble_512_in_the_benchmark_configuration(pkg, oracle_mod):
             want, _ = oracle_mod.run(states[i], j.seed, 0, 50, j.p)
             assert b.time(k) == 50
             assert np.array_equal(b.get_state(k), want), j.name
-        b.step(128)              # warm-up as in the benchmark: the automatic choice measures both kernels
+        b.step(256)              # warm-up as in the benchmark: the automatic choice measures its candidates
         b.synchronize()
-        b.step(2000 - 50 - 128)
+        b.step(2000 - 50 - 256)
         for i in sample:
             j = jobs[i]
             want, _ = oracle_mod.run(states[i], j.seed, 0, 2000, j.p)
