@@ -213,6 +213,7 @@ __device__ __forceinline__ uint32_t forced_mask(uint32_t cand, uint32_t u0, cons
         const int pos = __ffs(c) - 1;              // the lo-th candidate
         forced |= 1u << pos;
         cand = pos == 31 ? 0u : (cand & (0xFFFFFFFFu << (pos + 1)));
+        if (!cand) break;   // no candidate left: the next draw would decide nothing
         ++draw;
         u = more(draw);
     }
