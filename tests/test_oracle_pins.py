@@ -329,6 +329,22 @@ def test_forcing_thresholds_closed_form(oracle_mod):
     assert int(oracle_mod.forcing_thresholds(0.0)[32]) == 0
 
 
+def test_forcing_threshold_growth_bound():
+    """Q_K <= K (P + 1) for the integer recurrence (P = round(p 2^32)): each
+    floor step loses less than one unit, so Q_g - Q_{g-1} <= P + 1.  The GPU's
+    per-word pre-check rejects a word when u >= K (P + 1) on this bound, so a
+    violation would drop forcing events; checked here on the recurrence
+    itself for many p, including the rounding edges and p = 1."""
+    rng = np.random.Generator(np.random.PCG64(77))
+    ps = [0.0, 1.0, 1e-3, 5e-4, 0.5, 2.0 ** -32, 0.5 * 2.0 ** -32, 1.5 * 2.0 ** -32, 1 - 2.0 ** -32]
+    ps += list(rng.uniform(0, 1, 200)) + list(10.0 ** rng.uniform(-9, -1, 200))
+    for p in ps:
+        q = naive.thresholds(p)
+        P = q[1]            # Q_1 = 2^32 - floor(2^32 (2^32 - P) / 2^32) = P
+        for K in range(33):
+            assert q[K] <= K * (P + 1), (p, K)
+
+
 def test_forcing_p1_forces_every_candidate(oracle_mod):
     """With p = 1 no fluid node is left with bit 5 set and bit 2 clear."""
     import workloads
