@@ -97,7 +97,7 @@ __global__ void __launch_bounds__(kTmaThreads, SAT ? 1 : 2) fhp_step_tma_kernel(
     const StepVar v{a.dst, a.t_lo, a.t_hi};
     for (int i = 0; i < count; ++i) {
         const int s = i % kStages;
-        if (!mbar_wait_bounded(&full[s], (uint32_t)((i / kStages) & 1))) {
+        if (!mbar_wait_bounded_call(&full[s], (uint32_t)((i / kStages) & 1))) {
             if (lane == 0 && a.err) atomicOr(a.err, 1u);
             return;
         }

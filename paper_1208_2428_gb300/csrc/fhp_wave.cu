@@ -292,7 +292,7 @@ __global__ void __launch_bounds__(kWaveThreads, 1) fhp_wave_kernel(const StepArg
                     // is tested and the phase parity cannot alias.
                     for (int r = (i == p ? 0 : i); r <= i + 2 && ok; ++r) {
                         const uint32_t par = (uint32_t)((r / wa.D0) & 1);
-                        if (!mbar_try_wait(&full[r % wa.D0], par)) ok = mbar_wait_bounded(&full[r % wa.D0], par);
+                        ok = mbar_wait_bounded(&full[r % wa.D0], par);
                     }
                     ok = __all_sync(0xFFFFFFFFu, ok);
                     rm = ring0 + (size_t)(i % wa.D0) * slot0_words;
