@@ -265,12 +265,15 @@ def batched_vs_per_lattice(dev, stream, count: int, steps: int, per_steps: int, 
         for j, s0 in zip(jobs, states):
             k = b.add(j.W, j.H, j.seed, j.p)
             b.set_state(k, s0)
-        b.step(256)  # warm-up; the automatic choice times both kernels at two tile sizes here (64 steps each)
+        # warm-up; the automatic choice times its six candidates here (64 steps each): both kernels at two
+        # tile sizes, and blocked passes of 2 and 4 steps
+        b.step(384)
         b.synchronize()
         b.step(1)   # reads that measurement
         b.synchronize()
         tuned = b.tuned_kernel()
         tuned_quads = b.tile_quads
+        tuned_block = b.tuned_temporal_block()
         best = None
         for _ in range(repeats):
             l0 = b.kernel_launches
@@ -302,10 +305,12 @@ def batched_vs_per_lattice(dev, stream, count: int, steps: int, per_steps: int, 
         lat.close()
     per = nodes * per_steps / (ms_per / 1e3) / 1e9
     return {"lattices": count, "nodes": nodes, "batched_gsups": batched, "batched_steps": steps,
-            "batched_kernel": "fhp_batch_run_kernel" if tuned == 2 else "fhp_batch_kernel",
+            "batched_kernel": ("fhp_batch_block_kernel" if tuned_block > 1 else
+                               "fhp_batch_run_kernel" if tuned == 2 else "fhp_batch_kernel"),
             "batched_tile_quads": tuned_quads,
-            "tuned": {"kernel": tuned, "tile_quads": tuned_quads, "graph_steps": 64,
-                      "candidates": "single-step graphs / multi-step cooperative x 256 / 128 quads per tile"},
+            "tuned": {"kernel": tuned, "tile_quads": tuned_quads, "temporal_block": tuned_block, "graph_steps": 64,
+                      "candidates": "single-step graphs / multi-step cooperative x 256 / 128 quads per tile, "
+                                    "and blocked passes of 2 / 4 steps"},
             "batched_launches": launches_batched, "per_lattice_gsups": per, "per_lattice_steps": per_steps,
             "per_lattice_launches": launches_per, "speedup": batched / per,
             "batched_ms": best, "per_lattice_ms": ms_per}

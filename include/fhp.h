@@ -424,6 +424,33 @@ FHP_API int fhp_batch_get_tile_quads(const fhp_batch* batch);
  * kernels' work lists); -1 on error. */
 FHP_API int32_t fhp_batch_tile_count(fhp_batch* batch);
 
+/* Temporal blocking inside batches (the paper's kernels run one step per
+ * pass over the lattice; this is an alternative order of the same updates).
+ * With k = 2 or 4, each fhp_batch_step call advances every member whose rows
+ * are narrow enough (fhp_batch_block_rows > 0) by floor(s / k) passes of k
+ * steps, s = min(n, its budget): one launch per pass over tiles of full rows
+ * of all such members, each tile staged in shared memory with k extra rows
+ * above and below (periodic), stepped k times there and stored once.  The
+ * remaining steps (s mod k, all s for wider members) run on the batch step
+ * kernel.  Every member's state equals s single steps bit for bit.
+ * k = 1: no blocking.  k = 0 (default): automatic -- while the step kernel is
+ * AUTO, blocked passes of k = 2 and k = 4 (remainders on the single-step
+ * kernel) join the online tuning trial as two more candidates (c = 6, or 4
+ * with a fixed tile size) and the fastest candidate's temporal block is
+ * recorded with its kernel; otherwise none.  FHP_EINVAL for other values.
+ * fhp_batch_get_tuned_temporal_block: the block recorded for batches of
+ * `ntiles` tiles (0 = the current members; 0 = not yet measured, -1 for
+ * invalid arguments). */
+FHP_API int fhp_batch_set_temporal_block(fhp_batch* batch, int32_t k);
+FHP_API int fhp_batch_get_temporal_block(const fhp_batch* batch);
+FHP_API int fhp_batch_get_tuned_temporal_block(const fhp_batch* batch, int32_t ntiles);
+/* Output rows per blocked tile of a W x H member at temporal block k (2 or
+ * 4): the largest even R, at most H, whose R + 2k staged rows fit one staged
+ * plane of 3,072 words (a row is W / 32 words rounded up to a multiple of 4);
+ * 0 if the member takes no blocked passes: R would be below 4k (and below
+ * H), k is not 2 or 4, or the sizes are invalid. */
+FHP_API int fhp_batch_block_rows(int32_t width, int32_t height, int32_t k);
+
 /* Steps per captured CUDA graph of batch launches (0: launch directly).  The
  * graph reads the tile list and its length from device memory, so it is
  * captured once and survives members joining and leaving (it is captured

@@ -484,7 +484,7 @@ struct DeviceGuard {
 
 constexpr int kTuneClasses = 32;
 constexpr int kTuneMinSteps = 16;   // a trial runs at least this many steps with each candidate
-constexpr int kTuneCands = 4;       // (kernel, tile quads) pairs a trial compares
+constexpr int kTuneCands = 6;       // (kernel, tile quads, temporal block) candidates a trial compares
 constexpr int kDefaultTileQuads = 256;
 
 struct TuneTrial {
@@ -492,6 +492,7 @@ struct TuneTrial {
     int ncand = 0;
     int kind[kTuneCands] = {};
     int quads[kTuneCands] = {};
+    int block[kTuneCands] = {};      // temporal block k (1: none)
     cudaEvent_t ev[kTuneCands][2] = {};   // [candidate][start, end]
     double updates[kTuneCands] = {};
 };
@@ -513,7 +514,16 @@ struct fhp_batch {
     int step_kernel = FHP_BATCH_KERNEL_AUTO;
     int tuned[kTuneClasses] = {};               // per tile-count class: kernel measured fastest (0: unknown)
     int tuned_quads[kTuneClasses] = {};         // ... and its tile size (quads per tile)
+    int tuned_block[kTuneClasses] = {};         // ... and its temporal block (1: none)
     int tile_quads = 0;                         // quads per tile: 0 automatic (tuned with the kernel)
+    int temporal_block = 0;                     // 0 automatic (tuned with the kernel), 1 none, 2 or 4
+    // blocked passes: member table and tile list (allocated from the arena)
+    size_t bmem_off = SIZE_MAX, bmem_cap = 0;
+    size_t btile_off = SIZE_MAX, btile_cap = 0;
+    fhp::BlockMember* d_bmem = nullptr;
+    fhp::BlockTile* d_btiles = nullptr;
+    std::vector<fhp::BlockMember> h_bmem;
+    std::vector<fhp::BlockTile> h_btiles;
     int cur_quads = kDefaultTileQuads;          // tile size of the current tile list
     TuneTrial trial;
     int* d_step_base = nullptr;
@@ -993,7 +1003,29 @@ void apply_tile_quads(fhp_batch* b, int quads) {
 
 // Uploads the descriptors of a call of `chunk` steps (each member advances
 // min(chunk, its budget) steps); returns the largest count in *max_steps.
-int upload_descriptors(fhp_batch* b, int chunk, std::vector<int>& steps_of, int* max_steps) {
+// A member's step arguments at its current step (src: the buffer holding it).
+void fill_step_args(const fhp_batch* b, const Member& m, fhp::StepArgs& a) {
+    a.src = m.buf[m.cur];
+    a.dst = m.buf[m.cur ^ 1];
+    a.solid = m.solid;
+    a.plane_words = m.g.plane_words;
+    a.H = m.g.H;
+    a.Wq = m.g.Wq;
+    a.nq = m.g.nq;
+    a.Pq = m.g.Pq;
+    a.rows_per_warp = a.groups_per_parity = a.warps_per_row = 1;
+    a.key = fhp::Key2{(uint32_t)m.seed, (uint32_t)(m.seed >> 32)};
+    a.rest_rules = fhp::rest_rules_mask(m.g);
+    a.t_lo = (uint32_t)m.t;
+    a.t_hi = (uint32_t)(m.t >> 32);
+    a.err = b->d_err;
+    a.ft = m.ft;
+}
+
+// Descriptors of a call of `chunk` steps: member i advances by
+// min(chunk, its budget, caps[i] if caps is given) steps (steps_of[i]).
+int upload_descriptors(fhp_batch* b, int chunk, std::vector<int>& steps_of, int* max_steps,
+                       const std::vector<int>* caps = nullptr) {
     const size_t nm = b->members.size();
     b->h_lats.assign(nm, fhp::BatchLattice{});
     steps_of.assign(nm, 0);
@@ -1004,23 +1036,10 @@ int upload_descriptors(fhp_batch* b, int chunk, std::vector<int>& steps_of, int*
         if (!m.used) continue;
         int64_t k = chunk;
         if (m.steps_left >= 0 && m.steps_left < k) k = m.steps_left;
+        if (caps && (*caps)[i] < k) k = (*caps)[i];
         steps_of[i] = (int)k;
         *max_steps = std::max(*max_steps, (int)k);
-        L.a.src = m.buf[m.cur];
-        L.a.dst = m.buf[m.cur ^ 1];
-        L.a.solid = m.solid;
-        L.a.plane_words = m.g.plane_words;
-        L.a.H = m.g.H;
-        L.a.Wq = m.g.Wq;
-        L.a.nq = m.g.nq;
-        L.a.Pq = m.g.Pq;
-        L.a.rows_per_warp = L.a.groups_per_parity = L.a.warps_per_row = 1;
-        L.a.key = fhp::Key2{(uint32_t)m.seed, (uint32_t)(m.seed >> 32)};
-        L.a.rest_rules = fhp::rest_rules_mask(m.g);
-        L.a.t_lo = (uint32_t)m.t;
-        L.a.t_hi = (uint32_t)(m.t >> 32);
-        L.a.err = b->d_err;
-        L.a.ft = m.ft;
+        fill_step_args(b, m, L.a);
         L.ta.R = m.R;
         L.ta.ntiles = (m.g.H + m.R - 1) / m.R;
         L.ta.nq_magic = ((1ull << 32) + m.g.nq - 1) / m.g.nq;
@@ -1076,7 +1095,46 @@ int launch_run_call(fhp_batch* b, int max_steps) {
     return FHP_OK;
 }
 
-// max_steps launches of the single-step kernel, replayed from a captured
+// The graph of graph_steps launches of the single-step kernel is captured once (with one resident wave
+// of CTAs; those without a tile exit at once) and stays valid while the
+// membership changes: it reads the tile list and its length from device
+// memory.  It is dropped only when the device tables move.
+int ensure_graph(fhp_batch* b) {
+    if (b->graph || b->graph_steps <= 0) return FHP_OK;
+    cudaError_t e = cudaSuccess;
+    const int bps = fhp::batch_blocks_per_sm(b->device, &e);
+    if (e != cudaSuccess) return bcuda(b, e, "configuring the batch kernel");
+    int sms = 0;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
+    if (e != cudaSuccess) return bcuda(b, e, "querying the SM count");
+    const int full_grid = bps * sms;
+    const size_t smem = fhp::kBPrefixBytes + fhp::kBStages * fhp::kBStageBudget;
+    const int G = b->graph_steps;
+    cudaStream_t cs;
+    e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return bcuda(b, e, "creating the capture stream");
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        for (int o = 0; o < G; ++o)
+            fhp::fhp_batch_kernel<<<full_grid, fhp::kBThreads, smem, cs>>>(b->d_lats, b->d_tiles, b->d_step_base, o,
+                                                                            b->d_err);
+        fhp::advance_kernel<<<1, 32, 0, cs>>>(b->d_step_base, G);
+        e = cudaStreamEndCapture(cs, &graph);
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&b->graph, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    cudaStreamDestroy(cs);
+    if (e == cudaSuccess) e = cudaGraphUpload(b->graph, b->stream);  // not on the first replay's critical path
+    if (e != cudaSuccess) {
+        if (b->graph) cudaGraphExecDestroy(b->graph);
+        b->graph = nullptr;
+        return bcuda(b, e, "capturing the batch step graph");
+    }
+    return FHP_OK;
+}
+
+// max_steps launches of the single-step kernel, replayed from the captured
 // graph in groups of graph_steps.
 int launch_step_call(fhp_batch* b, int max_steps) {
     cudaError_t e = cudaSuccess;
@@ -1098,27 +1156,8 @@ int launch_step_call(fhp_batch* b, int max_steps) {
     int done = 0;
     const int G = b->graph_steps;
     if (G > 0 && max_steps >= G) {
-        if (!b->graph) {
-            cudaStream_t cs;
-            e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
-            if (e != cudaSuccess) return bcuda(b, e, "creating the capture stream");
-            cudaGraph_t graph = nullptr;
-            e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
-            if (e == cudaSuccess) {
-                for (int o = 0; o < G; ++o)
-                    fhp::fhp_batch_kernel<<<full_grid, fhp::kBThreads, smem, cs>>>(b->d_lats, b->d_tiles,
-                                                                                    b->d_step_base, o, b->d_err);
-                fhp::advance_kernel<<<1, 32, 0, cs>>>(b->d_step_base, G);
-                e = cudaStreamEndCapture(cs, &graph);
-            }
-            if (e == cudaSuccess) e = cudaGraphInstantiate(&b->graph, graph, 0);
-            if (graph) cudaGraphDestroy(graph);
-            cudaStreamDestroy(cs);
-            if (e != cudaSuccess) {
-                b->graph = nullptr;
-                return bcuda(b, e, "capturing the batch step graph");
-            }
-        }
+        const int rc = ensure_graph(b);
+        if (rc != FHP_OK) return rc;
         while (max_steps - done >= G) {
             e = cudaGraphLaunch(b->graph, b->stream);
             if (e != cudaSuccess) return bcuda(b, e, "launching the batch step graph");
@@ -1180,6 +1219,7 @@ void collect_trial(fhp_batch* b) {
     }
     b->tuned[tr.cls] = best >= 0 ? tr.kind[best] : FHP_BATCH_KERNEL_SINGLE_STEP;
     b->tuned_quads[tr.cls] = best >= 0 ? tr.quads[best] : kDefaultTileQuads;
+    b->tuned_block[tr.cls] = best >= 0 ? tr.block[best] : 1;
     tr.cls = -1;
 }
 
@@ -1193,16 +1233,111 @@ int ensure_trial_events(fhp_batch* b) {
     return FHP_OK;
 }
 
-// One chunk of steps with the given kernel.
-int run_chunk(fhp_batch* b, int chunk, int kind, std::vector<int>& steps_of, double* updates) {
+// One chunk of steps with the given kernel (member i at most caps[i] steps
+// if caps is given).
+int run_chunk(fhp_batch* b, int chunk, int kind, std::vector<int>& steps_of, double* updates,
+              const std::vector<int>* caps = nullptr) {
     int max_steps = 0;
-    int rc = upload_descriptors(b, chunk, steps_of, &max_steps);
+    int rc = upload_descriptors(b, chunk, steps_of, &max_steps, caps);
     if (rc != FHP_OK || max_steps == 0) return rc;
     rc = kind == FHP_BATCH_KERNEL_MULTI_STEP && max_steps >= 2 ? launch_run_call(b, max_steps)
                                                                : launch_step_call(b, max_steps);
     if (rc != FHP_OK) return rc;
     if (updates) *updates = issued_updates(b, steps_of);
     finish_call(b, steps_of);
+    return FHP_OK;
+}
+
+// Device tables of the blocked passes (member descriptors, tile list), grown
+// on demand from the arena; only work on the batch's stream uses them.
+int ensure_block_tables(fhp_batch* b, size_t nm, size_t ntiles) {
+    if (nm > b->bmem_cap) {
+        const size_t cap = std::max<size_t>(nm, 2 * b->bmem_cap + 16);
+        const size_t off = b->arena.allocate(cap * sizeof(fhp::BlockMember));
+        if (off == SIZE_MAX) return bfail(b, FHP_ENOMEM, "batch arena full (blocked-pass descriptors)");
+        if (b->bmem_off != SIZE_MAX) b->arena.release(b->bmem_off, b->bmem_cap * sizeof(fhp::BlockMember));
+        b->bmem_off = off;
+        b->bmem_cap = cap;
+        b->d_bmem = (fhp::BlockMember*)(b->arena_base + off);
+    }
+    if (ntiles > b->btile_cap) {
+        const size_t cap = std::max<size_t>(ntiles, 2 * b->btile_cap + 256);
+        const size_t off = b->arena.allocate(cap * sizeof(fhp::BlockTile));
+        if (off == SIZE_MAX) return bfail(b, FHP_ENOMEM, "batch arena full (blocked-pass tile list)");
+        if (b->btile_off != SIZE_MAX) b->arena.release(b->btile_off, b->btile_cap * sizeof(fhp::BlockTile));
+        b->btile_off = off;
+        b->btile_cap = cap;
+        b->d_btiles = (fhp::BlockTile*)(b->arena_base + off);
+    }
+    return FHP_OK;
+}
+
+// One chunk with temporal blocking k (2 or 4): every member whose rows fit a
+// blocked tile (fhp::batch_block_rows) advances by floor(s / k) passes of k
+// steps, s = min(chunk, its budget), one launch of the blocked kernel per
+// pass over the tiles of all such members; then the remaining steps of every
+// member (s mod k, or all s for members that take no pass) run on the batch
+// step kernel `kind`.  The result equals s single steps for every member.
+int run_blocked_chunk(fhp_batch* b, int chunk, int k, int kind, std::vector<int>& steps_of, double* updates) {
+    const size_t nm = b->members.size();
+    std::vector<int> passes(nm, 0), caps(nm, 0);
+    b->h_bmem.assign(nm, fhp::BlockMember{});
+    b->h_btiles.clear();
+    int max_passes = 0;
+    double upd = 0.0;
+    for (size_t i = 0; i < nm; ++i) {
+        const Member& m = b->members[i];
+        if (!m.used) continue;
+        int64_t s = chunk;
+        if (m.steps_left >= 0 && m.steps_left < s) s = m.steps_left;
+        upd += (double)m.g.W * m.g.H * (double)s;
+        const int R = fhp::batch_block_rows(m.g, k);
+        const int p = R > 0 ? (int)(s / k) : 0;
+        passes[i] = p;
+        caps[i] = (int)(s - (int64_t)p * k);
+        if (p == 0) continue;
+        max_passes = std::max(max_passes, p);
+        fhp::BlockMember& M = b->h_bmem[i];
+        fill_step_args(b, m, M.a);
+        M.buf[0] = m.buf[0];
+        M.buf[1] = m.buf[1];
+        M.t0 = (unsigned long long)m.t;
+        M.cur = m.cur;
+        M.passes = p;
+        M.R_out = R;
+        M.force = m.ft.q[32] != 0;
+        const int nt = (m.g.H + R - 1) / R;
+        for (int j = 0; j < nt; ++j) b->h_btiles.push_back(fhp::BlockTile{(int)i, j});
+    }
+    if (max_passes > 0) {
+        int rc = ensure_block_tables(b, nm, b->h_btiles.size());
+        if (rc != FHP_OK) return rc;
+        cudaError_t e = cudaMemcpyAsync(b->d_bmem, b->h_bmem.data(), nm * sizeof(fhp::BlockMember),
+                                        cudaMemcpyHostToDevice, b->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(b->d_btiles, b->h_btiles.data(), b->h_btiles.size() * sizeof(fhp::BlockTile),
+                                cudaMemcpyHostToDevice, b->stream);
+        if (e != cudaSuccess) return bcuda(b, e, "uploading the blocked-pass tables");
+        for (int p = 0; p < max_passes; ++p) {
+            e = fhp::launch_batch_block(b->d_bmem, b->d_btiles, (int)b->h_btiles.size(), p, k, b->d_err, b->stream);
+            if (e != cudaSuccess) return bcuda(b, e, "launching the blocked batch kernel");
+            ++b->launches;
+        }
+        for (size_t i = 0; i < nm; ++i) {
+            Member& m = b->members[i];
+            if (!m.used || passes[i] == 0) continue;
+            const int64_t adv = (int64_t)passes[i] * k;
+            m.t += adv;
+            m.cur ^= passes[i] & 1;   // one write per pass
+            if (m.steps_left >= 0) m.steps_left -= adv;
+        }
+    }
+    std::vector<int> rest_of;
+    int rc = run_chunk(b, chunk, kind, rest_of, nullptr, &caps);
+    if (rc != FHP_OK) return rc;
+    steps_of.assign(nm, 0);
+    for (size_t i = 0; i < nm; ++i) steps_of[i] = passes[i] * k + (i < rest_of.size() ? rest_of[i] : 0);
+    if (updates) *updates = upd;
     return FHP_OK;
 }
 
@@ -1237,9 +1372,11 @@ int batch_step(fhp_batch* b, int64_t n) {
     if (b->step_kernel == FHP_BATCH_KERNEL_AUTO && b->ntiles > 0) {
         collect_trial(b);
         // Candidates: both kernels, and with an automatic tile size two
-        // sizes (256 and 128 quads per tile).  A trial needs parts long
-        // enough for the single-step kernel to run as it normally does (from
-        // the captured graph).
+        // sizes (256 and 128 quads per tile); with an automatic temporal
+        // block also blocked passes of k = 2 and k = 4 steps (remainders on
+        // the single-step kernel).  A trial needs parts long enough for the
+        // single-step kernel to run as it normally does (from the captured
+        // graph).
         TuneTrial& tr = b->trial;
         int nc = 0;
         const int sizes[2] = {kDefaultTileQuads, kDefaultTileQuads / 2};
@@ -1247,6 +1384,14 @@ int batch_step(fhp_batch* b, int64_t n) {
             for (int kind : {FHP_BATCH_KERNEL_SINGLE_STEP, FHP_BATCH_KERNEL_MULTI_STEP}) {
                 tr.kind[nc] = kind;
                 tr.quads[nc] = b->tile_quads ? b->tile_quads : sizes[si];
+                tr.block[nc] = b->temporal_block > 1 ? b->temporal_block : 1;
+                ++nc;
+            }
+        if (b->temporal_block == 0)
+            for (int k : {2, 4}) {
+                tr.kind[nc] = FHP_BATCH_KERNEL_SINGLE_STEP;
+                tr.quads[nc] = b->tile_quads ? b->tile_quads : kDefaultTileQuads;
+                tr.block[nc] = k;
                 ++nc;
             }
         const int64_t min_part = std::max<int64_t>(kTuneMinSteps, b->graph_steps);
@@ -1254,7 +1399,28 @@ int batch_step(fhp_batch* b, int64_t n) {
             // A trial: an equal part of the call with each candidate.
             rc = ensure_trial_events(b);
             if (rc != FHP_OK) return rc;
-            const int part = (int)std::min<int64_t>(n / nc, (int64_t)1 << 20);
+            // One-time host work stays out of the timed parts: the device
+            // tables are grown to the largest candidate tiling first (growing
+            // them drops the graph), then the graph is captured and both
+            // kernels are configured.  Capturing inside a part once made the
+            // single-step kernel look slower than it is (64 lattices: 2356
+            // GSUPS for the multi-step kernel was chosen over 2756).
+            for (int k = 0; k < nc; ++k) {
+                apply_tile_quads(b, tr.quads[k]);
+                rc = prepare_tiles(b);
+                if (rc != FHP_OK) return rc;
+            }
+            rc = ensure_graph(b);
+            if (rc != FHP_OK) return rc;
+            {
+                cudaError_t e = cudaSuccess;
+                (void)fhp::batch_run_blocks_per_sm(b->device, &e);
+                if (e == cudaSuccess) e = fhp::configure_batch_block();
+                if (e != cudaSuccess) return bcuda(b, e, "configuring the batch kernels");
+            }
+            // Parts of a multiple of 4 steps: blocked candidates then run no
+            // remainder steps.
+            const int part = (int)(std::min<int64_t>(n / nc, (int64_t)1 << 20) & ~(int64_t)3);
             tr.ncand = nc;
             for (int k = 0; k < nc; ++k) {
                 apply_tile_quads(b, tr.quads[k]);
@@ -1262,7 +1428,8 @@ int batch_step(fhp_batch* b, int64_t n) {
                 if (rc != FHP_OK) return rc;
                 cudaEventRecord(tr.ev[k][0], b->stream);
                 tr.updates[k] = 0.0;
-                rc = run_chunk(b, part, tr.kind[k], steps_of, &tr.updates[k]);
+                rc = tr.block[k] > 1 ? run_blocked_chunk(b, part, tr.block[k], tr.kind[k], steps_of, &tr.updates[k])
+                                     : run_chunk(b, part, tr.kind[k], steps_of, &tr.updates[k]);
                 if (rc != FHP_OK) return rc;
                 cudaError_t e = cudaEventRecord(tr.ev[k][1], b->stream);
                 if (e != cudaSuccess) return bcuda(b, e, "recording the tuning events");
@@ -1290,7 +1457,11 @@ int batch_step(fhp_batch* b, int64_t n) {
             const int t = b->tuned[cls];
             kind = t == FHP_BATCH_KERNEL_AUTO ? FHP_BATCH_KERNEL_SINGLE_STEP : t;
         }
-        rc = run_chunk(b, chunk, kind, steps_of, nullptr);
+        // Temporal block: the caller's, else (with the automatic kernel) the
+        // one recorded for the class, else none.
+        int k = b->temporal_block;
+        if (k == 0) k = (b->step_kernel == FHP_BATCH_KERNEL_AUTO && b->tuned_block[cls]) ? b->tuned_block[cls] : 1;
+        rc = k > 1 ? run_blocked_chunk(b, chunk, k, kind, steps_of, nullptr) : run_chunk(b, chunk, kind, steps_of, nullptr);
         if (rc != FHP_OK) return rc;
         left -= chunk;
     }
@@ -1317,6 +1488,25 @@ int fhp_batch_set_tile_quads(fhp_batch* b, int32_t quads) {
 }
 
 int fhp_batch_get_tile_quads(const fhp_batch* b) { return b ? b->cur_quads : -1; }
+
+int fhp_batch_set_temporal_block(fhp_batch* b, int32_t k) {
+    if (!b || (k != 0 && k != 1 && k != 2 && k != 4))
+        return bfail(b, FHP_EINVAL, "batch temporal block %d not in {0, 1, 2, 4}", k);
+    b->temporal_block = k;
+    return FHP_OK;
+}
+
+int fhp_batch_get_temporal_block(const fhp_batch* b) { return b ? b->temporal_block : -1; }
+
+int fhp_batch_get_tuned_temporal_block(const fhp_batch* b, int32_t ntiles) {
+    if (!b || ntiles < 0) return -1;
+    return b->tuned_block[tile_class(ntiles ? ntiles : tiles_at(b, kDefaultTileQuads))];
+}
+
+int fhp_batch_block_rows(int32_t width, int32_t height, int32_t k) {
+    if (width < 32 || width % 32 || height < 2 || height % 2) return 0;
+    return fhp::batch_block_rows(fhp::make_geometry(width, height), k);
+}
 
 int32_t fhp_batch_tile_count(fhp_batch* b) {
     if (!b) return -1;
@@ -1367,8 +1557,9 @@ int fhp_batch_synchronize(fhp_batch* b) {
     if (word) {
         cudaMemset(b->d_err, 0, sizeof word);
         if (word & fhp::kErrBounds)
-            return bfail(b, FHP_EDEBUG, "a debug-build index check failed (site %u); the access was skipped",
-                         (word >> 8) & 0xFFu);
+            return bfail(b, FHP_EDEBUG,
+                         "a debug-build index check failed (site %u, value %u, error word 0x%08x); the access "
+                         "was skipped", (word >> 8) & 0xFFu, word >> 16, word);
         return bfail(b, FHP_ETIMEOUT, "a batch kernel gave up waiting for its input copies");
     }
     return FHP_OK;

@@ -27,6 +27,10 @@ enum DebugSite : unsigned int {
     kSiteWaveQuad = 7,       // wavefront ring words a quad reads or writes
     kSiteBlockStage = 8,     // 2-D tile kernel: staged rows and quads
     kSiteBatchTile = 9,      // batch tile record within its member
+    kSiteBatchBlock = 10,    // batch temporal blocking: a tile record within its member
+    kSiteBatchBlockStage = 11,  // ... staged row and word of a copy
+    kSiteBatchBlockHeader = 12, // ... a tile's staged rows within a plane
+    kSiteBatchBlockQuad = 13,   // ... rows and words a quad reads
     kSiteSelfTest = 99,      // fhp_debug_selftest
 };
 
@@ -48,6 +52,25 @@ __device__ __forceinline__ bool dbg_ok(bool cond, unsigned int* err, unsigned in
     (void)cond;
     (void)err;
     (void)site;
+    return true;
+}
+
+// As dbg_ok, and the first failure of a launch also leaves `value` (16 bits)
+// in bits 16..31 of the error word.
+__device__ __forceinline__ bool dbg_ok_v(bool cond, unsigned int* err, unsigned int site, unsigned int value) {
+#ifdef FHP_DEBUG
+    if (!cond) {
+        if (err) {
+            const unsigned int word = kErrBounds | (site << 8) | ((value & 0xFFFFu) << 16);
+            if (atomicCAS(err, 0u, word) != 0u) atomicOr(err, kErrBounds | (site << 8));
+        }
+        return false;
+    }
+#endif
+    (void)cond;
+    (void)err;
+    (void)site;
+    (void)value;
     return true;
 }
 

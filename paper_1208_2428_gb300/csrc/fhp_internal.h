@@ -127,6 +127,33 @@ cudaError_t launch_block(const Geometry& g, const uint32_t* src, uint32_t* dst, 
                          bool has_solid, bool force, const ForcingTable& ft, Key2 key, uint64_t t0, int k,
                          cudaStream_t stream, unsigned int* err);
 
+// Temporal blocking inside batches (fhp_batch_block.cu): one launch applies
+// pass `pass` (k = 2 or 4 steps) to every member with more passes than that
+// in the call, tile by tile over a list of (member, row tile) records.  A
+// member's tile holds R_out full rows (even; batch_block_rows, 0 if the
+// member's rows are too wide); the kernel stages R_out + 2k rows of the
+// member's pitch in each of 16 shared-memory planes of kBBPlaneWords words.
+constexpr int kBBPlaneWords = 3072;
+struct BlockMember {
+    StepArgs a;              // geometry, solid plane, key, forcing, rules, err (src, dst, t: set per pass)
+    uint32_t* buf[2];        // state buffers; buf[cur] holds the state at step t0
+    unsigned long long t0;   // the member's step at the start of the call
+    int cur;
+    int passes;              // blocked passes of the member in the call
+    int R_out;               // output rows per tile
+    int force;               // forcing probability nonzero
+    int y0, rows_out, active;  // per tile: filled in by the kernel in its shared-memory copy
+    int pad;
+};
+struct BlockTile {
+    int lattice;             // index into the member table
+    int tile;                // row tile of the member
+};
+int batch_block_rows(const Geometry& g, int k);
+cudaError_t configure_batch_block();   // kernel attributes of the current device (first use loads the kernel)
+cudaError_t launch_batch_block(const BlockMember* d_members, const BlockTile* d_tiles, int ntiles, int pass, int k,
+                               unsigned int* err, cudaStream_t stream);
+
 // Temporal blocking by row wavefronts (fhp_wave.cu): k (2, 3 or 4) steps from
 // src (state at t0) to dst in one pass over full-width row bands, the
 // intermediate levels in shared-memory row rings.  Supported when a row of

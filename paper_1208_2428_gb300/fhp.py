@@ -121,6 +121,10 @@ def load(path: str | None = None):
         "fhp_batch_get_tuned_tile_quads": (ctypes.c_int, [vp, i32]),
         "fhp_batch_set_tile_quads": (ctypes.c_int, [vp, i32]),
         "fhp_batch_get_tile_quads": (ctypes.c_int, [vp]),
+        "fhp_batch_set_temporal_block": (ctypes.c_int, [vp, i32]),
+        "fhp_batch_get_temporal_block": (ctypes.c_int, [vp]),
+        "fhp_batch_get_tuned_temporal_block": (ctypes.c_int, [vp, i32]),
+        "fhp_batch_block_rows": (ctypes.c_int, [i32, i32, i32]),
         "fhp_batch_tile_count": (i32, [vp]),
         "fhp_batch_load_obstacles": (ctypes.c_int, [vp, i32, u8p]),
         "fhp_batch_lattice_bytes": (ctypes.c_size_t, [i32, i32]),
@@ -457,6 +461,11 @@ class Batch:
     def lattice_bytes(width: int, height: int) -> int:
         return int(load().fhp_batch_lattice_bytes(int(width), int(height)))
 
+    @staticmethod
+    def block_rows(width: int, height: int, k: int) -> int:
+        """Output rows per blocked tile of a member at temporal block k (0: it takes no blocked passes)."""
+        return int(load().fhp_batch_block_rows(int(width), int(height), int(k)))
+
     def add(self, width: int, height: int, seed: int = 0, forcing_p: float = 0.0) -> int:
         slot = ctypes.c_int32(-1)
         self._check(self._lib.fhp_batch_add(self._h, int(width), int(height), int(seed) & (2**64 - 1),
@@ -580,6 +589,20 @@ class Batch:
 
     def set_graph_steps(self, n: int):
         self._check(self._lib.fhp_batch_set_graph_steps(self._h, int(n)))
+
+    def set_temporal_block(self, k: int):
+        """Steps per blocked pass: 2 or 4, 1 = none, 0 = tuned online with the kernel."""
+        self._check(self._lib.fhp_batch_set_temporal_block(self._h, int(k)))
+
+    @property
+    def temporal_block(self) -> int:
+        """The temporal-block setting (0: automatic)."""
+        return int(self._lib.fhp_batch_get_temporal_block(self._h))
+
+    def tuned_temporal_block(self, ntiles: int | None = None) -> int:
+        """Temporal block the automatic choice recorded for this batch's size class (0: not yet)."""
+        n = 0 if ntiles is None else int(ntiles)
+        return int(self._lib.fhp_batch_get_tuned_temporal_block(self._h, n))
 
     def coarse_grain(self, slot: int, block: int = 32):
         H, W = self.shapes[slot]

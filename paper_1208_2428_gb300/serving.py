@@ -140,6 +140,11 @@ class Server:
             raise ValueError("need 1 <= quantum_min <= quantum_max")
         self.batch = batch if batch is not None else Batch(hbm_budget, device=device, stream=stream)
         self.batch.set_graph_steps(graph_steps)
+        # Quanta are too short for blocked passes to pay or for a tuning trial
+        # over them (six parts of at least 16 steps); the kernel and tile size
+        # are still tuned online within a 64-step quantum.
+        if hasattr(self.batch, "set_temporal_block"):
+            self.batch.set_temporal_block(1)
         self.hbm_budget = int(hbm_budget)
         self.quantum_max = int(quantum_max)
         self.quantum_min = int(quantum_min)

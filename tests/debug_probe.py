@@ -68,34 +68,35 @@ def main() -> int:
         assert lat.debug_canaries() == (6, 0)
     c_ref, _, _, _ = oracle.coarse_grain(s0, 32)
     assert np.array_equal(counts, c_ref)
-    # batches: both kernels and every tile size
-    jobs = [(96, 6, 0.0), (160, 10, 0.2), (512, 4, 0.05), (4128, 8, 0.0), (64, 2, 0.3)]
-    for kind in (1, 2):
-        for quads in (64, 256):
-            arena = sum(Batch.lattice_bytes(w, h) for w, h, _ in jobs) + (8 << 20)
-            with Batch(arena) as b:
-                b.set_step_kernel(kind)
-                b.set_tile_quads(quads)
-                slots, states = [], []
-                for i, (w, h, pp) in enumerate(jobs):
-                    rng = np.random.Generator(np.random.PCG64(70 + i))
-                    s = workloads.bernoulli_lattice(w, h, 0.35, 70 + i, workloads.random_points(w, h, 0.05, rng))
-                    slot = b.add(w, h, 70 + i, pp)
-                    b.set_state(slot, s)
-                    slots.append(slot)
-                    states.append(s)
-                b.step(7)
-                b.synchronize()
-                for i, (w, h, pp) in enumerate(jobs):
-                    want, _ = oracle.run(states[i], 70 + i, 0, 7, pp)
-                    if not np.array_equal(b.get_state(slots[i]), want):
-                        print(json.dumps({"ok": False, "case": ["batch", kind, quads, w, h], "why": "state"}))
-                        return 1
-                checked, corrupted = b.debug_canaries()
-                if checked != len(jobs) or corrupted:
-                    print(json.dumps({"ok": False, "case": ["batch", kind, quads], "why": "canaries"}))
+    # batches: both kernels, two tile sizes, and blocked passes of 2 and 4 steps
+    jobs = [(96, 6, 0.0), (160, 10, 0.2), (512, 4, 0.05), (4128, 8, 0.0), (64, 2, 0.3), (12288, 8, 0.1)]
+    for kind, quads, block in ((1, 64, 1), (1, 256, 1), (2, 64, 1), (2, 256, 1), (1, 256, 2), (1, 256, 4),
+                               (2, 64, 4)):
+        arena = sum(Batch.lattice_bytes(w, h) for w, h, _ in jobs) + (8 << 20)
+        with Batch(arena) as b:
+            b.set_step_kernel(kind)
+            b.set_tile_quads(quads)
+            b.set_temporal_block(block)
+            slots, states = [], []
+            for i, (w, h, pp) in enumerate(jobs):
+                rng = np.random.Generator(np.random.PCG64(70 + i))
+                s = workloads.bernoulli_lattice(w, h, 0.35, 70 + i, workloads.random_points(w, h, 0.05, rng))
+                slot = b.add(w, h, 70 + i, pp)
+                b.set_state(slot, s)
+                slots.append(slot)
+                states.append(s)
+            b.step(7)
+            b.synchronize()
+            for i, (w, h, pp) in enumerate(jobs):
+                want, _ = oracle.run(states[i], 70 + i, 0, 7, pp)
+                if not np.array_equal(b.get_state(slots[i]), want):
+                    print(json.dumps({"ok": False, "case": ["batch", kind, quads, block, w, h], "why": "state"}))
                     return 1
-                cases += 1
+            checked, corrupted = b.debug_canaries()
+            if checked != len(jobs) or corrupted:
+                print(json.dumps({"ok": False, "case": ["batch", kind, quads, block], "why": "canaries"}))
+                return 1
+            cases += 1
     print(json.dumps({"ok": True, "cases": cases, "selftest": selftest}))
     return 0
 

@@ -184,9 +184,10 @@ def test_multi_step_kernel_edge_cases(pkg, oracle_mod):
 
 def test_automatic_choice_is_tuned_online_and_exact(pkg, oracle_mod):
     """The automatic choice times both kernels at two tile sizes (256 and 128
-    quads per tile) on a first long call (a quarter of its steps each) and
-    records the fastest pair for the batch's size class; members stay
-    bit-exact throughout, across the re-tiling."""
+    quads per tile) and blocked passes of 2 and 4 steps on a first long call
+    (a sixth of its steps each) and records the fastest candidate for the
+    batch's size class; members stay bit-exact throughout, across the
+    re-tiling and the blocked passes."""
     jobs = small_ensemble(10, 5)
     states = [j.initial_state() for j in jobs]
     arena = sum(pkg.Batch.lattice_bytes(j.W, j.H) for j in jobs) + (64 << 20)
@@ -203,17 +204,22 @@ def test_automatic_choice_is_tuned_online_and_exact(pkg, oracle_mod):
         b.synchronize()
         b.step(1)
         assert b.tuned_kernel() == 0
-        b.step(64)                 # a trial: 16 steps with each (kernel, tile size)
+        b.step(95)
+        b.synchronize()
+        b.step(1)
+        assert b.tuned_kernel() == 0   # 95 steps: too short for six parts of 16
+        b.step(96)                 # a trial: 16 steps with each (kernel, tile size) and blocked k = 2, 4
         b.synchronize()
         b.step(3)                  # reads the trial's events
         assert b.tuned_kernel() in (1, 2)
         assert b.tuned_tile_quads() in (128, 256)
+        assert b.tuned_temporal_block() in (1, 2, 4)
         assert b.tile_quads == b.tuned_tile_quads()
         b.step(6)
         b.synchronize()
         for j, s0, k in zip(jobs, states, slots):
-            want, _ = oracle_mod.run(s0, j.seed, 0, 88, j.p)
-            assert b.time(k) == 88
+            want, _ = oracle_mod.run(s0, j.seed, 0, 216, j.p)
+            assert b.time(k) == 216
             assert np.array_equal(b.get_state(k), want), j.name
 
 
@@ -268,11 +274,91 @@ def test_ensemble_512_in_the_benchmark_configuration(pkg, oracle_mod):
             want, _ = oracle_mod.run(states[i], j.seed, 0, 50, j.p)
             assert b.time(k) == 50
             assert np.array_equal(b.get_state(k), want), j.name
-        b.step(256)              # warm-up as in the benchmark: the automatic choice measures its candidates
+        b.step(384)              # warm-up as in the benchmark: the automatic choice measures its candidates
         b.synchronize()
-        b.step(2000 - 50 - 256)
+        b.step(2000 - 50 - 384)
         for i in sample:
             j = jobs[i]
             want, _ = oracle_mod.run(states[i], j.seed, 0, 2000, j.p)
             assert b.time(slots[i]) == 2000
             assert np.array_equal(b.get_state(slots[i]), want), (j.name, j.W, j.H)
+
+
+@pytest.mark.parametrize("k", [2, 4])
+def test_batch_temporal_block_matches_oracle(pkg, oracle_mod, k):
+    """Blocked passes of k steps inside a batch (tiles of full rows stepped k
+    times in shared memory): members too wide for a blocked tile, a ragged
+    row, a 2-row lattice, a tall narrow one, FHP-I members, step budgets that
+    end between passes, calls that are not multiples of k and a start step
+    that is not either -- every member equals its oracle run alone."""
+    jobs = small_ensemble(10, 21) + [
+        workloads.Lattice("w8192", 8192, 20, 0.3, 31, 0.05, 0, obstacle="points", point_frac=0.01),
+        workloads.Lattice("w12288", 12288, 8, 0.3, 35, 0.02, 0),
+        workloads.Lattice("narrow", 32, 8, 0.4, 32, 0.02, 0),
+        workloads.Lattice("ragged", 160, 50, 0.3, 33, 0.01, 0, obstacle="walls"),
+        workloads.Lattice("tall", 96, 1030, 0.25, 34, 0.0, 0, obstacle="points", point_frac=0.02),
+        workloads.Lattice("short", 640, 2, 0.3, 36, 0.03, 0),
+    ]
+    states = [j.initial_state() for j in jobs]
+    budgets = [-1] * len(jobs)
+    budgets[1], budgets[4], budgets[-3] = 5, 22, 9
+    rules = [2] * len(jobs)
+    rules[2] = rules[-2] = 1
+    blocked = [pkg.Batch.block_rows(j.W, j.H, k) > 0 for j in jobs]
+    assert not blocked[11] and blocked[12] and blocked[13] and blocked[14] and blocked[15]
+    assert blocked[10] == (k == 2)
+    arena = sum(pkg.Batch.lattice_bytes(j.W, j.H) for j in jobs) + (64 << 20)
+    with pkg.Batch(arena) as b:
+        b.set_temporal_block(k)
+        assert b.temporal_block == k
+        b.set_step_kernel(1)
+        b.set_graph_steps(4)
+        slots = []
+        for j, s0, bud, ru in zip(jobs, states, budgets, rules):
+            s = b.add(j.W, j.H, j.seed, j.p)
+            b.set_state(s, s0)
+            b.set_time(s, 3)
+            if ru != 2:
+                b.set_rules(s, ru)
+            if bud >= 0:
+                b.set_steps_left(s, bud)
+            slots.append(s)
+        l0 = b.kernel_launches
+        b.step(13)
+        b.step(10)
+        b.synchronize()
+        assert b.kernel_launches - l0 < 2 * 23   # blocked passes replace k launches each
+        for j, s0, bud, ru, s in zip(jobs, states, budgets, rules, slots):
+            n = 23 if bud < 0 else min(bud, 23)
+            assert b.time(s) == 3 + n, j.name
+            want, _ = oracle_mod.run(s0, j.seed, 3, n, j.p, rules=ru)
+            got = b.get_state(s)
+            assert np.array_equal(got, want), (j.name, j.W, j.H, k, int((got != want).sum()))
+        with pytest.raises(pkg.FhpError):
+            b.set_temporal_block(3)
+
+
+def test_batch_temporal_block_with_multi_step_remainders(pkg, oracle_mod):
+    """Temporal block 4 with the multi-step kernel for the remaining steps,
+    switched off again between calls: the members still equal their oracle
+    runs."""
+    jobs = small_ensemble(8, 23)
+    states = [j.initial_state() for j in jobs]
+    arena = sum(pkg.Batch.lattice_bytes(j.W, j.H) for j in jobs) + (64 << 20)
+    with pkg.Batch(arena) as b:
+        b.set_step_kernel(2)
+        b.set_temporal_block(4)
+        slots = []
+        for j, s0 in zip(jobs, states):
+            s = b.add(j.W, j.H, j.seed, j.p)
+            b.set_state(s, s0)
+            slots.append(s)
+        b.step(19)
+        b.set_temporal_block(1)
+        b.step(6)
+        b.set_temporal_block(2)
+        b.step(7)
+        b.synchronize()
+        for j, s0, s in zip(jobs, states, slots):
+            want, _ = oracle_mod.run(s0, j.seed, 0, 32, j.p)
+            assert np.array_equal(b.get_state(s), want), j.name
