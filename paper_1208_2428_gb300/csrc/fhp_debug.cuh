@@ -27,10 +27,9 @@ enum DebugSite : unsigned int {
     kSiteWaveQuad = 7,       // wavefront ring words a quad reads or writes
     kSiteBlockStage = 8,     // 2-D tile kernel: staged rows and quads
     kSiteBatchTile = 9,      // batch tile record within its member
-    kSiteBatchBlock = 10,    // batch temporal blocking: a tile record within its member
-    kSiteBatchBlockStage = 11,  // ... staged row and word of a copy
-    kSiteBatchBlockHeader = 12, // ... a tile's staged rows within a plane
-    kSiteBatchBlockQuad = 13,   // ... rows and words a quad reads
+    kSiteBatchBlockHeader = 10, // batch temporal blocking: a tile within its member, its rows within a plane
+    kSiteBatchBlockStage = 11,  // ... the rows of a bulk copy within the staged plane
+    kSiteBatchBlockQuad = 12,   // ... the rows and words a quad reads
     kSiteSelfTest = 99,      // fhp_debug_selftest
 };
 
