@@ -1310,6 +1310,16 @@ int run_blocked_chunk(fhp_batch* b, int chunk, int k, int kind, std::vector<int>
         for (int j = 0; j < nt; ++j) b->h_btiles.push_back(fhp::BlockTile{(int)i, j});
     }
     if (max_passes > 0) {
+        // CTA c takes tiles c, c + grid, ...: with the list ordered by
+        // decreasing work (quads of a pass), every CTA's share comes out about
+        // even and the last tiles of a pass are the small ones.
+        auto work = [&](const fhp::BlockTile& t) {
+            const fhp::BlockMember& M = b->h_bmem[t.lattice];
+            const int rows_out = std::min(M.R_out, M.a.H - t.tile * M.R_out);
+            return (long long)(rows_out + k) * M.a.nq;
+        };
+        std::stable_sort(b->h_btiles.begin(), b->h_btiles.end(),
+                         [&](const fhp::BlockTile& x, const fhp::BlockTile& y) { return work(x) > work(y); });
         int rc = ensure_block_tables(b, nm, b->h_btiles.size());
         if (rc != FHP_OK) return rc;
         cudaError_t e = cudaMemcpyAsync(b->d_bmem, b->h_bmem.data(), nm * sizeof(fhp::BlockMember),

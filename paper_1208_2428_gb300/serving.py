@@ -129,22 +129,26 @@ class Server:
     runs min(quantum_max, fewest steps any resident lattice still needs), but
     at least quantum_min, so that short requests finish close to their last
     step while long ones share launches.  ``graph_steps`` is the length of the
-    captured CUDA graph of batch launches.  ``batch`` substitutes another
-    object with the :class:`Batch` interface (the scheduling tests use a
-    host-only stand-in)."""
+    captured CUDA graph of batch launches.  ``temporal_block`` (1, 2 or 4)
+    is the batch's temporal block.  ``batch`` substitutes another object with
+    the :class:`Batch` interface (the scheduling tests use a host-only
+    stand-in)."""
 
     def __init__(self, hbm_budget: int, quantum_max: int = 64, quantum_min: int = 8, graph_steps: int = 16,
                  device=None, stream=None, clock: Callable[[], float] | None = None, batch=None,
-                 time_device: bool = False, pipeline: bool = True):
+                 time_device: bool = False, pipeline: bool = True, temporal_block: int = 1):
         if quantum_min < 1 or quantum_max < quantum_min:
             raise ValueError("need 1 <= quantum_min <= quantum_max")
         self.batch = batch if batch is not None else Batch(hbm_budget, device=device, stream=stream)
         self.batch.set_graph_steps(graph_steps)
-        # Quanta are too short for blocked passes to pay or for a tuning trial
-        # over them (six parts of at least 16 steps); the kernel and tile size
-        # are still tuned online within a 64-step quantum.
+        # Temporal block of the batch: quanta (8..64 steps) are too short for a
+        # tuning trial that includes blocked passes (six parts of at least 16
+        # steps), so it is set here -- 1 (no blocking, the default) or 2 / 4
+        # (blocked passes for the lattices narrow enough, the rest of each
+        # quantum on the step kernel); the kernel and tile size are still tuned
+        # online within a quantum.
         if hasattr(self.batch, "set_temporal_block"):
-            self.batch.set_temporal_block(1)
+            self.batch.set_temporal_block(int(temporal_block))
         self.hbm_budget = int(hbm_budget)
         self.quantum_max = int(quantum_max)
         self.quantum_min = int(quantum_min)

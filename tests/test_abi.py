@@ -67,3 +67,27 @@ def test_debug_build_exports_every_declared_symbol():
     dbg.fhp_required_bytes.argtypes = [ctypes.c_int32, ctypes.c_int32]
     rel = fhp.load()
     assert dbg.fhp_required_bytes(256, 64) == rel.fhp_required_bytes(256, 64) + 6 * 256
+
+
+def test_batch_block_rows_without_gpu(lib):
+    """Blocked tiles inside batches (host arithmetic only): R_out + 2k staged
+    rows of the member's row pitch fill at most one 3,072-word plane, R_out is
+    even (or the whole lattice), at most H, and at least 4k rows -- else the
+    member takes no blocked passes."""
+    for W in range(32, 16385, 32):
+        Pq = 4 * ((W // 32 + 3) // 4)
+        for H in (2, 4, 8, 20, 64, 130, 1030, 2048):
+            for k in (2, 4):
+                R = lib.fhp_batch_block_rows(W, H, k)
+                if R == 0:
+                    full = (3072 // Pq - 2 * k) & ~1
+                    assert min(full, H) < 4 * k and min(full, H) != H or full <= 0, (W, H, k)
+                    continue
+                assert (min(R, H) + 2 * k) * Pq <= 3072, (W, H, k, R)
+                assert R <= H and (R % 2 == 0 or R == H) and (R >= 4 * k or R == H), (W, H, k, R)
+                # the largest such R: two more rows would not fit (or exceed H)
+                assert R == H or (R + 2 + 2 * k) * Pq > 3072, (W, H, k, R)
+    assert lib.fhp_batch_block_rows(2048, 2048, 4) == 40
+    assert lib.fhp_batch_block_rows(16384, 4096, 2) == 0
+    assert lib.fhp_batch_block_rows(2048, 512, 3) == 0
+    assert lib.fhp_batch_block_rows(100, 64, 2) == 0
