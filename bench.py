@@ -48,6 +48,10 @@ def parse_args():
                                            "serving"],
                     default="cylinder")
     ap.add_argument("--ensemble-size", type=int, default=512, help="lattices of the ensemble workload")
+    ap.add_argument("--batch-step-kernel", type=int, default=0, choices=[0, 1, 2],
+                    help="batch step kernel of the ensemble workload (0: tuned online)")
+    ap.add_argument("--batch-temporal-block", type=int, default=0, choices=[0, 1, 2, 4],
+                    help="batch temporal block of the ensemble workload (0: tuned online)")
     ap.add_argument("--serving-jobs", type=int, default=2000, help="requests of the serving trace")
     ap.add_argument("--serving-budget-gb", type=float, default=80.0, help="HBM budget of the serving arena")
     ap.add_argument("--no-serving-compare", action="store_true",
@@ -247,7 +251,8 @@ def cpu_baseline(job, s0, target_seconds: float):
             "one_thread": single, "cpu_model": cpu_model()}
 
 
-def batched_vs_per_lattice(dev, stream, count: int, steps: int, per_steps: int, repeats: int = 1):
+def batched_vs_per_lattice(dev, stream, count: int, steps: int, per_steps: int, repeats: int = 1,
+                           step_kernel: int = 0, temporal_block: int = 0):
     """Aggregate GSUPS of `count` ensemble lattices (sides 128..2048, 1 %
     point obstacles, per-lattice seeds and densities) advanced (a) as one
     batch -- one launch per step over all lattices, CUDA-graph replays -- and
@@ -262,6 +267,8 @@ def batched_vs_per_lattice(dev, stream, count: int, steps: int, per_steps: int, 
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with Batch(arena, device=dev, stream=stream) as b:
         b.set_graph_steps(64)
+        b.set_step_kernel(step_kernel)
+        b.set_temporal_block(temporal_block)
         for j, s0 in zip(jobs, states):
             k = b.add(j.W, j.H, j.seed, j.p)
             b.set_state(k, s0)
@@ -271,9 +278,9 @@ def batched_vs_per_lattice(dev, stream, count: int, steps: int, per_steps: int, 
         b.synchronize()
         b.step(1)   # reads that measurement
         b.synchronize()
-        tuned = b.tuned_kernel()
+        tuned = b.tuned_kernel() if step_kernel == 0 else step_kernel
         tuned_quads = b.tile_quads
-        tuned_block = b.tuned_temporal_block()
+        tuned_block = temporal_block if temporal_block else (b.tuned_temporal_block() if step_kernel == 0 else 1)
         best = None
         for _ in range(repeats):
             l0 = b.kernel_launches
@@ -309,6 +316,7 @@ def batched_vs_per_lattice(dev, stream, count: int, steps: int, per_steps: int, 
                                "fhp_batch_run_kernel" if tuned == 2 else "fhp_batch_kernel"),
             "batched_tile_quads": tuned_quads,
             "tuned": {"kernel": tuned, "tile_quads": tuned_quads, "temporal_block": tuned_block, "graph_steps": 64,
+                      "set_by_flags": bool(step_kernel or temporal_block),
                       "candidates": "single-step graphs / multi-step cooperative x 256 / 128 quads per tile, "
                                     "and blocked passes of 2 / 4 steps"},
             "batched_launches": launches_batched, "per_lattice_gsups": per, "per_lattice_steps": per_steps,
@@ -326,7 +334,8 @@ def run_ensemble(args):
     steps = args.lattice_steps or 2000
     sampler = ClockSampler(local)
     sampler.start()
-    r = batched_vs_per_lattice(dev, stream, args.ensemble_size, steps, min(steps, 200), repeats=max(1, args.steps))
+    r = batched_vs_per_lattice(dev, stream, args.ensemble_size, steps, min(steps, 200), repeats=max(1, args.steps),
+                               step_kernel=args.batch_step_kernel, temporal_block=args.batch_temporal_block)
     clocks = sampler.stop()
     peak, peak_src = measured_hbm_peak()
     bytes_per_node = 15 / 8.0

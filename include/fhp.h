@@ -323,7 +323,9 @@ FHP_API int fhp_philox4x32_10_device(const uint32_t* device_ctr, const uint32_t*
  * between calls, while the others keep their state.  fhp_batch_step(n)
  * advances every member by min(n, its remaining budget) steps; each step is
  * one kernel launch over the tiles of all members (replayed from a captured
- * CUDA graph), and every member evolves exactly as it would alone.
+ * CUDA graph), or each pass of k steps one launch of the blocked kernel
+ * (fhp_batch_set_temporal_block), and every member evolves exactly as it
+ * would alone.
  * Slots are small integers, reused after fhp_batch_remove.  Calls on one
  * batch must not overlap in time.  Errors: FHP_EINVAL for bad slots or
  * arguments, FHP_ENOMEM when the arena cannot hold a new member (admission
@@ -391,16 +393,19 @@ FHP_API int fhp_batch_step(fhp_batch* batch, int64_t n);
  * a tile is staged for step s once the tiles of step s - 1 it reads (itself
  * and its two neighbours in its lattice) are finished, tracked by per-tile
  * counters.  AUTO (default): autotuned online together with the tile size
- * -- batches are classed by the binary order of magnitude of their tile
- * count at the default size of 256 quads (128-node units) per tile; the
- * first call in a class of at least c * max(16, graph steps) steps runs an
- * equal part of its steps with each of c candidates -- both kernels, and,
- * while the tile size is automatic (fhp_batch_set_tile_quads), tiles of 256
- * and of 128 quads (c = 4; else c = 2) -- timed with CUDA events on the
- * batch's stream, and a later call records the candidate with the most node
- * updates per millisecond for the class (read without waiting); until then
- * SINGLE_STEP with 256-quad tiles runs.  Results are identical for every
- * choice. */
+ * and the temporal block -- batches are classed by the binary order of
+ * magnitude of their tile count at the default size of 256 quads (128-node
+ * units) per tile; the first call in a class of at least
+ * c * max(16, graph steps) steps runs an equal part of its steps (rounded
+ * down to a multiple of 4) with each of c candidates -- both kernels; while
+ * the tile size is automatic (fhp_batch_set_tile_quads), tiles of 256 and of
+ * 128 quads; while the temporal block is automatic, blocked passes of 2 and
+ * of 4 steps (c = 6 with both automatic) -- timed with CUDA events on the
+ * batch's stream after the one-time set-up of every candidate (graph
+ * capture, device tables, kernel attributes), and a later call records the
+ * candidate with the most node updates per millisecond for the class (read
+ * without waiting); until then SINGLE_STEP with 256-quad tiles and no
+ * blocking runs.  Results are identical for every choice. */
 #define FHP_BATCH_KERNEL_AUTO 0
 #define FHP_BATCH_KERNEL_SINGLE_STEP 1
 #define FHP_BATCH_KERNEL_MULTI_STEP 2
