@@ -443,6 +443,10 @@ FHP_API int32_t fhp_batch_tile_count(fhp_batch* batch);
  * kernel) join the online tuning trial as two more candidates (c = 6, or 4
  * with a fixed tile size) and the fastest candidate's temporal block is
  * recorded with its kernel; otherwise none.  FHP_EINVAL for other values.
+ * Blocked passes take a descriptor table (about 0.4 KB per member slot) and
+ * a tile list (12 bytes per tile) from the arena: with k = 2 or 4 a call
+ * fails with FHP_ENOMEM if the arena cannot hold them; the automatic choice
+ * then tunes without the blocked candidates.
  * fhp_batch_get_tuned_temporal_block: the block recorded for batches of
  * `ntiles` tiles (0 = the current members; 0 = not yet measured, -1 for
  * invalid arguments). */

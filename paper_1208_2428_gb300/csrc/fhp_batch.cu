@@ -1272,6 +1272,26 @@ int ensure_block_tables(fhp_batch* b, size_t nm, size_t ntiles) {
     return FHP_OK;
 }
 
+// Make room for the blocked passes' tables of the current members (k = 4
+// has the most tiles).  Returns false, leaving the batch's error message as
+// it was, if the arena cannot hold them: the automatic choice then tunes
+// without blocked candidates instead of failing the call.
+bool reserve_block_tables(fhp_batch* b) {
+    size_t tiles = 0;
+    for (const Member& m : b->members) {
+        if (!m.used) continue;
+        const int R = fhp::batch_block_rows(m.g, 4);
+        if (R > 0) tiles += (size_t)((m.g.H + R - 1) / R);
+    }
+    if (tiles == 0) return false;
+    const std::string saved = b->err;
+    if (ensure_block_tables(b, b->members.size(), tiles) != FHP_OK) {
+        b->err = saved;
+        return false;
+    }
+    return true;
+}
+
 // One chunk with temporal blocking k (2 or 4): every member whose rows fit a
 // blocked tile (fhp::batch_block_rows) advances by floor(s / k) passes of k
 // steps, s = min(chunk, its budget), one launch of the blocked kernel per
@@ -1397,15 +1417,28 @@ int batch_step(fhp_batch* b, int64_t n) {
                 tr.block[nc] = b->temporal_block > 1 ? b->temporal_block : 1;
                 ++nc;
             }
-        if (b->temporal_block == 0)
-            for (int k : {2, 4}) {
-                tr.kind[nc] = FHP_BATCH_KERNEL_SINGLE_STEP;
-                tr.quads[nc] = b->tile_quads ? b->tile_quads : kDefaultTileQuads;
-                tr.block[nc] = k;
-                ++nc;
-            }
         const int64_t min_part = std::max<int64_t>(kTuneMinSteps, b->graph_steps);
-        if (b->tuned[cls] == FHP_BATCH_KERNEL_AUTO && tr.cls < 0 && n >= nc * min_part) {
+        bool trial = false;
+        if (b->tuned[cls] == FHP_BATCH_KERNEL_AUTO && tr.cls < 0) {
+            if (b->temporal_block == 0) {
+                // A call long enough for all candidates; the blocked ones need
+                // their tables in the arena, and without room for them the
+                // trial goes on with the others.
+                if (n >= (nc + 2) * min_part) {
+                    trial = true;
+                    if (reserve_block_tables(b))
+                        for (int k : {2, 4}) {
+                            tr.kind[nc] = FHP_BATCH_KERNEL_SINGLE_STEP;
+                            tr.quads[nc] = b->tile_quads ? b->tile_quads : kDefaultTileQuads;
+                            tr.block[nc] = k;
+                            ++nc;
+                        }
+                }
+            } else {
+                trial = n >= nc * min_part;
+            }
+        }
+        if (trial) {
             // A trial: an equal part of the call with each candidate.
             rc = ensure_trial_events(b);
             if (rc != FHP_OK) return rc;

@@ -362,3 +362,37 @@ def test_batch_temporal_block_with_multi_step_remainders(pkg, oracle_mod):
         for j, s0, s in zip(jobs, states, slots):
             want, _ = oracle_mod.run(s0, j.seed, 0, 32, j.p)
             assert np.array_equal(b.get_state(s), want), j.name
+
+
+def test_automatic_choice_without_room_for_blocked_tables(pkg, oracle_mod):
+    """An arena too full for the blocked passes' tables: a call long enough
+    for a trial (six parts of 16 steps) tunes without the blocked candidates
+    instead of failing, and the members stay exact."""
+    job = workloads.Lattice("tight", 256, 192, 0.3, 78, 0.01, 0, obstacle="walls")
+    s0 = job.initial_state()
+    need = pkg.Batch.lattice_bytes(job.W, job.H)
+    with pkg.Batch(4 * need) as b:
+        b.set_graph_steps(8)
+        k = b.add(job.W, job.H, job.seed, job.p)
+        b.set_state(k, s0)
+        b.step(1)                                  # the kernels' tables are in place
+        fillers = []
+        for w, h, tries in ((256, 192, 8), (128, 64, 8), (32, 2, 8)):
+            for _ in range(tries):
+                if b.count >= 16:                  # the descriptor table holds 16 members without growing
+                    break
+                try:
+                    fillers.append(b.add(w, h, 5, 0.0))
+                except pkg.FhpError as e:
+                    assert e.code == 2             # FHP_ENOMEM
+                    break
+        assert b.free_bytes < 6 << 10, b.free_bytes   # less than one blocked-pass descriptor table
+        assert b.tuned_kernel() == 0
+        b.step(96)                                 # a trial: four parts of 24 steps, no blocked candidates
+        b.synchronize()
+        b.step(1)
+        assert b.tuned_kernel() in (1, 2)
+        assert b.tuned_temporal_block() == 1
+        b.remove(fillers[0])                       # room for the read-back staging (W x H bytes)
+        want, _ = oracle_mod.run(s0, job.seed, 0, 98, job.p)
+        assert np.array_equal(b.get_state(k), want)
