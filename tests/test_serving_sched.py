@@ -34,6 +34,9 @@ class FakeBatch:
     def set_graph_steps(self, n):
         self.graph = n
 
+    def set_temporal_block(self, k):
+        self.temporal_block = k
+
     def add(self, w, h, seed, p):
         need = self.lattice_bytes(w, h)
         if need > self.free_bytes:
@@ -193,3 +196,14 @@ def test_pipelined_ticks_keep_one_quantum_queued():
     assert steps[0] < steps[1] < read1          # quantum 2 was queued before request 1 was read back
     assert ("remove", 1) in fake.log[read1:]
     assert [c.request.seed for c in sorted(done, key=lambda c: c.finished)] == [1, 2]
+
+
+def test_server_sets_the_batch_temporal_block():
+    """Blocking stays off unless asked for: quanta are too short for a tuning
+    trial over the blocked passes."""
+    b = FakeBatch(1 << 20)
+    Server(1 << 20, batch=b)
+    assert b.temporal_block == 1
+    b4 = FakeBatch(1 << 20)
+    Server(1 << 20, batch=b4, temporal_block=4)
+    assert b4.temporal_block == 4
