@@ -61,6 +61,8 @@ def parse_args():
     ap.add_argument("--lattice-steps", type=int, default=None,
                     help="time steps per benchmark step (default: the workload's run length)")
     ap.add_argument("--temporal-block", type=int, default=1)
+    ap.add_argument("--temporal-block-kernel", type=int, default=0, choices=[0, 1, 2],
+                    help="blocked kernel for --temporal-block > 1: 0 automatic, 1 row wavefronts, 2 2-D tiles")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the automatic kernel choice instead of timing the configurations first")
     ap.add_argument("--step-kernel", type=int, default=0,
@@ -540,6 +542,8 @@ def run_gpu(args):
     lat.set_state(s0)
     lat.set_rules(args.rules)
     lat.set_temporal_block(args.temporal_block)
+    if args.temporal_block_kernel:
+        lat.set_temporal_block_kernel(args.temporal_block_kernel)
     lat.set_step_kernel(args.step_kernel)
     tuned = None
     if not args.no_autotune and args.step_kernel == 0 and args.temporal_block == 1:
